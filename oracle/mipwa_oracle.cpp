@@ -1,0 +1,466 @@
+// MIPWA oracle: a plain, slow, FP64 CPU statement of what the hot path computes.
+//
+// TEST INFRASTRUCTURE ONLY. Nothing in the product library links, includes or
+// calls this file; only the test suite, the smoke check and the timed CPU
+// baseline of the benchmark load it. It shares no code, header or constant
+// table with the CUDA path.
+//
+// Every function follows the definitions of arXiv:1703.03284 and the
+// textbook conventions the paper cites for its amplitudes:
+//   * Eq. 1 (Sec. 2): A(s12,s13) = sum_L sum_k c_k^L A_k^L(s12,s13), truncated at L = 2.
+//   * Sec. 2: spin-dependent relativistic Breit-Wigner times a real angular factor
+//     (the CLEO convention the paper cites): Blatt-Weisskopf barriers, running width,
+//     Zemach tensors.
+//   * Sec. 2: MIPWA S-wave A0(s) = a0(s) exp(i phi0(s)), with (a_k, phi_k) at the N
+//     boundary points and a cubic spline in between (natural boundary conditions:
+//     magnitude and phase splined separately).
+//   * Sec. 4: Bose symmetrisation along both m^2(h+h-) axes.
+//   * Sec. 2 / Sec. 4: unbinned -2 ln L with a normalisation integral taken as the
+//     mean of |A|^2 over a phase-space sample (evenly spaced grid or uniform MC).
+//
+// Arithmetic is IEEE double everywhere, complex numbers are std::complex<double>,
+// sums over events are Neumaier-compensated over fixed chunks of events so the
+// result does not depend on the thread count.
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef std::complex<double> cplx;
+
+extern "C" {
+
+#define ORACLE_MAX_RES 8
+#define ORACLE_MAX_KNOTS 128
+
+// Decay D -> h1 h2 h3 with m3 == m2 (the two identical particles); resonances in
+// the (1,2) pair (and, by Bose symmetry, in the (1,3) pair).
+typedef struct {
+  double mD, m1, m2;                 // masses in GeV; m3 = m2
+  int n_res;                         // number of Breit-Wigner terms
+  double mass[ORACLE_MAX_RES];       // resonance pole masses m_r
+  double width[ORACLE_MAX_RES];      // nominal widths Gamma_r
+  int spin[ORACLE_MAX_RES];          // L = 0, 1, 2
+  int n_knots;                       // N >= 2 spline boundary points
+  double knots[ORACLE_MAX_KNOTS];    // strictly increasing s_k (GeV^2)
+  double r_res, r_D;                 // Blatt-Weisskopf radii (1/GeV)
+} oracle_model;
+
+enum { ORACLE_OK = 0, ORACLE_EINVAL = -1, ORACLE_ENONPOS = -3 };
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- kinematics
+// Kallen function lambda(x, a^2, b^2) written in its factored form.
+static double kallen(double x, double a, double b) {
+  return (x - (a + b) * (a + b)) * (x - (a - b) * (a - b));
+}
+
+// Breakup momentum of the pair (1,2) in its rest frame at invariant mass^2 s.
+static double q_of(const oracle_model* md, double s) {
+  return std::sqrt(kallen(s, md->m1, md->m2)) / (2.0 * std::sqrt(s));
+}
+
+// Momentum of the bachelor (particle 3) in the rest frame of the (1,2) pair.
+static double p_of(const oracle_model* md, double s) {
+  return std::sqrt(kallen(s, md->mD, md->m2)) / (2.0 * std::sqrt(s));
+}
+
+static double sum_m2(const oracle_model* md) {
+  return md->mD * md->mD + md->m1 * md->m1 + 2.0 * md->m2 * md->m2;
+}
+
+// Dalitz-plot boundary: range of s23 at fixed s12 (PDG kinematics, energies of
+// particles 2 and 3 in the (1,2) rest frame).
+static void s23_range(const oracle_model* md, double s12, double* lo, double* hi) {
+  const double m1 = md->m1, m2 = md->m2, m3 = md->m2, M = md->mD;
+  const double rs = std::sqrt(s12);
+  const double E2 = (s12 - m1 * m1 + m2 * m2) / (2.0 * rs);
+  const double E3 = (M * M - s12 - m3 * m3) / (2.0 * rs);
+  const double k2 = std::sqrt(std::fmax(E2 * E2 - m2 * m2, 0.0));
+  const double k3 = std::sqrt(std::fmax(E3 * E3 - m3 * m3, 0.0));
+  *lo = (E2 + E3) * (E2 + E3) - (k2 + k3) * (k2 + k3);
+  *hi = (E2 + E3) * (E2 + E3) - (k2 - k3) * (k2 - k3);
+}
+
+static int inside(const oracle_model* md, double s12, double s13) {
+  const double smin = (md->m1 + md->m2) * (md->m1 + md->m2);
+  const double smax = (md->mD - md->m2) * (md->mD - md->m2);
+  if (!(s12 > smin && s12 < smax)) return 0;
+  if (!(s13 > smin && s13 < smax)) return 0;
+  double lo, hi;
+  s23_range(md, s12, &lo, &hi);
+  const double s23 = sum_m2(md) - s12 - s13;
+  return (s23 >= lo && s23 <= hi) ? 1 : 0;
+}
+
+// ------------------------------------------------- Breit-Wigner building blocks
+// Blatt-Weisskopf barrier factor normalised to 1 at z = z0, z = (r k)^2.
+static double barrier(int L, double z, double z0) {
+  if (L == 0) return 1.0;
+  if (L == 1) return std::sqrt((1.0 + z0) / (1.0 + z));
+  return std::sqrt((z0 * z0 + 3.0 * z0 + 9.0) / (z * z + 3.0 * z + 9.0));
+}
+
+// Zemach angular factor for a resonance in the pair (1,2) at invariant s, with
+// s_other the (1,3) invariant. Equals (-4 p q cos theta13)^L-type tensors:
+// Z1 = -4 p q cos(theta), Z2 = 16 p^2 q^2 (cos^2(theta) - 1/3).
+static double zemach(const oracle_model* md, int L, double s, double s_other) {
+  if (L == 0) return 1.0;
+  const double M2 = md->mD * md->mD, m1s = md->m1 * md->m1, m2s = md->m2 * md->m2,
+               m3s = md->m2 * md->m2;
+  const double s23 = sum_m2(md) - s - s_other;
+  const double z1 = s_other - s23 + (M2 - m3s) * (m2s - m1s) / s;
+  if (L == 1) return z1;
+  const double four_p2 = s - 2.0 * M2 - 2.0 * m3s + (M2 - m3s) * (M2 - m3s) / s;
+  const double four_q2 = s - 2.0 * m1s - 2.0 * m2s + (m1s - m2s) * (m1s - m2s) / s;
+  return z1 * z1 - four_p2 * four_q2 / 3.0;
+}
+
+// Relativistic Breit-Wigner propagator with running width:
+// T(s) = 1 / (m^2 - s - i m Gamma(s)),
+// Gamma(s) = Gamma_r (q/q0)^(2L+1) (m/sqrt s) F_R(s)^2.
+static cplx propagator(const oracle_model* md, int r, double s) {
+  const int L = md->spin[r];
+  const double m = md->mass[r], G = md->width[r];
+  const double q = q_of(md, s), q0 = q_of(md, m * m);
+  const double rr = md->r_res;
+  const double FR = barrier(L, rr * rr * q * q, rr * rr * q0 * q0);
+  const double gam = G * std::pow(q / q0, 2 * L + 1) * (m / std::sqrt(s)) * FR * FR;
+  return 1.0 / cplx(m * m - s, -m * gam);
+}
+
+// One resonance term A_r(s, s_other) = F_R F_D Z_L T, resonance in the pair whose
+// invariant is s.
+static cplx resonance(const oracle_model* md, int r, double s, double s_other) {
+  const int L = md->spin[r];
+  const double m = md->mass[r];
+  const double q = q_of(md, s), q0 = q_of(md, m * m);
+  const double p = p_of(md, s), p0 = p_of(md, m * m);
+  const double rr = md->r_res, rd = md->r_D;
+  const double FR = barrier(L, rr * rr * q * q, rr * rr * q0 * q0);
+  const double FD = barrier(L, rd * rd * p * p, rd * rd * p0 * p0);
+  return FR * FD * zemach(md, L, s, s_other) * propagator(md, r, s);
+}
+
+// -------------------------------------------------------------- natural spline
+// Second derivatives M_k of the natural cubic spline through (x_k, y_k):
+// M_0 = M_{n-1} = 0 and, for interior k,
+// h_{k-1}/6 M_{k-1} + (h_{k-1}+h_k)/3 M_k + h_k/6 M_{k+1}
+//   = (y_{k+1}-y_k)/h_k - (y_k-y_{k-1})/h_{k-1}.
+// Solved with the Thomas algorithm (tridiagonal Gaussian elimination).
+static void spline_second_derivs(int n, const double* x, const double* y, double* M) {
+  for (int k = 0; k < n; ++k) M[k] = 0.0;
+  if (n < 3) return;
+  const int m = n - 2;
+  std::vector<double> sub(m), dia(m), sup(m), rhs(m);
+  for (int k = 1; k <= n - 2; ++k) {
+    const double hl = x[k] - x[k - 1], hr = x[k + 1] - x[k];
+    sub[k - 1] = hl / 6.0;
+    dia[k - 1] = (hl + hr) / 3.0;
+    sup[k - 1] = hr / 6.0;
+    rhs[k - 1] = (y[k + 1] - y[k]) / hr - (y[k] - y[k - 1]) / hl;
+  }
+  for (int i = 1; i < m; ++i) {
+    const double w = sub[i] / dia[i - 1];
+    dia[i] -= w * sup[i - 1];
+    rhs[i] -= w * rhs[i - 1];
+  }
+  M[m] = rhs[m - 1] / dia[m - 1];
+  for (int i = m - 2; i >= 0; --i) M[i + 1] = (rhs[i] - sup[i] * M[i + 2]) / dia[i];
+}
+
+// Segment holding s; the first and last segments continue beyond the end knots.
+static int spline_segment(int n, const double* x, double s) {
+  int j = 0;
+  while (j < n - 2 && s >= x[j + 1]) ++j;
+  return j;
+}
+
+static double spline_eval(int n, const double* x, const double* y, const double* M,
+                          double s) {
+  const int j = spline_segment(n, x, s);
+  const double h = x[j + 1] - x[j];
+  const double A = x[j + 1] - s, B = s - x[j];
+  return M[j] * A * A * A / (6.0 * h) + M[j + 1] * B * B * B / (6.0 * h) +
+         (y[j] / h - M[j] * h / 6.0) * A + (y[j + 1] / h - M[j + 1] * h / 6.0) * B;
+}
+
+// ------------------------------------------------------------ full amplitude
+struct Evaluator {
+  const oracle_model* md;
+  int R, N;
+  std::vector<cplx> c;          // BW coefficients c_r
+  std::vector<double> a, phi;   // knot magnitudes and phases
+  std::vector<double> Ma, Mphi; // their spline second derivatives
+  // For the gradient: second derivatives of the spline through the unit vector e_k.
+  std::vector<std::vector<double>> Munit;
+
+  Evaluator(const oracle_model* m, const double* params, bool want_unit) : md(m) {
+    R = md->n_res;
+    N = md->n_knots;
+    c.resize(R);
+    for (int r = 0; r < R; ++r) c[r] = cplx(params[2 * r], params[2 * r + 1]);
+    a.assign(params + 2 * R, params + 2 * R + N);
+    phi.assign(params + 2 * R + N, params + 2 * R + 2 * N);
+    Ma.resize(N);
+    Mphi.resize(N);
+    spline_second_derivs(N, md->knots, a.data(), Ma.data());
+    spline_second_derivs(N, md->knots, phi.data(), Mphi.data());
+    if (want_unit) {
+      Munit.assign(N, std::vector<double>(N));
+      std::vector<double> e(N);
+      for (int k = 0; k < N; ++k) {
+        for (int i = 0; i < N; ++i) e[i] = (i == k) ? 1.0 : 0.0;
+        spline_second_derivs(N, md->knots, e.data(), Munit[k].data());
+      }
+    }
+  }
+
+  // Bose-symmetrised basis of resonance r: A_r(s12,s13) + A_r(s13,s12).
+  cplx basis(int r, double s12, double s13) const {
+    return resonance(md, r, s12, s13) + resonance(md, r, s13, s12);
+  }
+
+  cplx swave(double s) const {
+    const double mag = spline_eval(N, md->knots, a.data(), Ma.data(), s);
+    const double ph = spline_eval(N, md->knots, phi.data(), Mphi.data(), s);
+    return mag * cplx(std::cos(ph), std::sin(ph));
+  }
+
+  cplx amp(double s12, double s13) const {
+    cplx A(0.0, 0.0);
+    for (int r = 0; r < R; ++r) A += c[r] * basis(r, s12, s13);
+    A += swave(s12) + swave(s13);
+    return A;
+  }
+
+  // d|A|^2/d(theta) for every parameter theta, written into g (length 2R+2N).
+  void amp2_grad(double s12, double s13, cplx A, double* g) const {
+    for (int r = 0; r < R; ++r) {
+      const cplx B = basis(r, s12, s13);
+      g[2 * r] = 2.0 * std::real(std::conj(A) * B);
+      g[2 * r + 1] = 2.0 * std::real(std::conj(A) * cplx(0.0, 1.0) * B);
+    }
+    for (int k = 0; k < 2 * N; ++k) g[2 * R + k] = 0.0;
+    const double ss[2] = {s12, s13};
+    std::vector<double> e(N, 0.0);
+    for (int ch = 0; ch < 2; ++ch) {
+      const double s = ss[ch];
+      const double mag = spline_eval(N, md->knots, a.data(), Ma.data(), s);
+      const double ph = spline_eval(N, md->knots, phi.data(), Mphi.data(), s);
+      const cplx u(std::cos(ph), std::sin(ph));
+      // dA/da(s) = u ; dA/dphi(s) = i a(s) u
+      const double da = 2.0 * std::real(std::conj(A) * u);
+      const double dphi = 2.0 * std::real(std::conj(A) * cplx(0.0, 1.0) * mag * u);
+      for (int k = 0; k < N; ++k) {
+        e[k] = 1.0;
+        const double w = spline_eval(N, md->knots, e.data(), Munit[k].data(), s);
+        e[k] = 0.0;
+        g[2 * R + k] += da * w;
+        g[2 * R + N + k] += dphi * w;
+      }
+    }
+  }
+};
+
+// Neumaier-compensated accumulator.
+struct CSum {
+  double s = 0.0, c = 0.0;
+  void add(double x) {
+    const double t = s + x;
+    if (std::fabs(s) >= std::fabs(x))
+      c += (s - t) + x;
+    else
+      c += (x - t) + s;
+    s = t;
+  }
+  double value() const { return s + c; }
+};
+
+static const int64_t kChunk = 4096;
+
+static int valid_model(const oracle_model* md) {
+  if (!md) return 0;
+  if (md->n_res < 0 || md->n_res > ORACLE_MAX_RES) return 0;
+  if (md->n_knots < 2 || md->n_knots > ORACLE_MAX_KNOTS) return 0;
+  for (int k = 1; k < md->n_knots; ++k)
+    if (!(md->knots[k] > md->knots[k - 1])) return 0;
+  for (int r = 0; r < md->n_res; ++r)
+    if (md->spin[r] < 0 || md->spin[r] > 2) return 0;
+  return 1;
+}
+
+extern "C" {
+
+int oracle_max_res(void) { return ORACLE_MAX_RES; }
+int oracle_max_knots(void) { return ORACLE_MAX_KNOTS; }
+
+// --- pieces exposed for the closed-form tests ---
+double oracle_q(const oracle_model* md, double s) { return q_of(md, s); }
+double oracle_p(const oracle_model* md, double s) { return p_of(md, s); }
+void oracle_s23_range(const oracle_model* md, double s12, double* lo, double* hi) {
+  s23_range(md, s12, lo, hi);
+}
+double oracle_barrier(int L, double z, double z0) { return barrier(L, z, z0); }
+double oracle_zemach(const oracle_model* md, int L, double s, double s_other) {
+  return zemach(md, L, s, s_other);
+}
+void oracle_propagator(const oracle_model* md, int r, double s, double* re, double* im) {
+  const cplx T = propagator(md, r, s);
+  *re = T.real();
+  *im = T.imag();
+}
+void oracle_resonance(const oracle_model* md, int r, double s, double s_other, double* re,
+                      double* im) {
+  const cplx A = resonance(md, r, s, s_other);
+  *re = A.real();
+  *im = A.imag();
+}
+void oracle_spline_second_derivs(int n, const double* x, const double* y, double* M) {
+  spline_second_derivs(n, x, y, M);
+}
+void oracle_spline_eval(int n, const double* x, const double* y, const double* M,
+                        int64_t ns, const double* s, double* out) {
+  for (int64_t i = 0; i < ns; ++i) out[i] = spline_eval(n, x, y, M, s[i]);
+}
+
+// inside[i] = 1 when (s12,s13) lies inside the Dalitz plot.
+int oracle_inside(const oracle_model* md, int64_t n, const double* s12s13, uint8_t* out,
+                  int nthreads) {
+  (void)nthreads;
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int64_t i = 0; i < n; ++i) out[i] = (uint8_t)inside(md, s12s13[2 * i], s12s13[2 * i + 1]);
+  return ORACLE_OK;
+}
+
+// Complex amplitude A(s12,s13) (Eq. 1 with the Bose-symmetrised terms).
+int oracle_amp(const oracle_model* md, const double* params, int64_t n, const double* s12s13,
+               double* re, double* im) {
+  if (!valid_model(md)) return ORACLE_EINVAL;
+  Evaluator ev(md, params, false);
+  for (int64_t i = 0; i < n; ++i) {
+    const cplx A = ev.amp(s12s13[2 * i], s12s13[2 * i + 1]);
+    re[i] = A.real();
+    im[i] = A.imag();
+  }
+  return ORACLE_OK;
+}
+
+// Symmetrised Breit-Wigner basis B_r for every event: out[(i*R + r)*2 + {0,1}].
+int oracle_basis(const oracle_model* md, int64_t n, const double* s12s13, double* out) {
+  if (!valid_model(md)) return ORACLE_EINVAL;
+  std::vector<double> dummy(2 * md->n_res + 2 * md->n_knots, 0.0);
+  Evaluator ev(md, dummy.data(), false);
+  for (int64_t i = 0; i < n; ++i)
+    for (int r = 0; r < md->n_res; ++r) {
+      const cplx B = ev.basis(r, s12s13[2 * i], s12s13[2 * i + 1]);
+      out[(i * md->n_res + r) * 2] = B.real();
+      out[(i * md->n_res + r) * 2 + 1] = B.imag();
+    }
+  return ORACLE_OK;
+}
+
+// PDF density |A|^2 inside the Dalitz plot and 0 outside it.
+int oracle_density(const oracle_model* md, const double* params, int64_t n,
+                   const double* s12s13, double* out, int nthreads) {
+  if (!valid_model(md)) return ORACLE_EINVAL;
+  Evaluator ev(md, params, false);
+  (void)nthreads;
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int64_t i = 0; i < n; ++i) {
+    const double s12 = s12s13[2 * i], s13 = s12s13[2 * i + 1];
+    out[i] = inside(md, s12, s13) ? std::norm(ev.amp(s12, s13)) : 0.0;
+  }
+  return ORACLE_OK;
+}
+
+// -2 ln L = -2 sum_i ln|A(x_i)|^2 + 2 N_data ln I,  I = (1/N_norm) sum_j |A(y_j)|^2.
+// When grad != NULL it also receives d(-2 ln L)/d(params), the analytic adjoint.
+int oracle_nll_grad(const oracle_model* md, const double* params, int64_t n_data,
+                    const double* data, int64_t n_norm, const double* norm, double* nll,
+                    double* grad, int nthreads) {
+  if (!valid_model(md) || n_norm <= 0 || n_data < 0) return ORACLE_EINVAL;
+  const bool want_grad = grad != nullptr;
+  Evaluator ev(md, params, want_grad);
+  const int P = 2 * md->n_res + 2 * md->n_knots;
+  const int nth = nthreads > 0 ? nthreads : 1;
+
+  // Each chunk of kChunk events is summed on its own, then the chunk sums are
+  // combined in chunk order: the result is independent of the thread count.
+  auto run = [&](int64_t n, const double* ev_xy, bool is_data, CSum* total, CSum* gtot,
+                 int* bad) {
+    const int64_t nchunk = (n + kChunk - 1) / kChunk;
+    std::vector<double> csum(nchunk);
+    std::vector<double> cgrad(want_grad ? nchunk * P : 0);
+    std::vector<int> cbad(nchunk, 0);
+    (void)nth;
+#pragma omp parallel for schedule(static) num_threads(nth)
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+      CSum s;
+      std::vector<CSum> gs(want_grad ? P : 0);
+      std::vector<double> g(want_grad ? P : 0);
+      const int64_t i1 = std::min(n, (ch + 1) * kChunk);
+      for (int64_t i = ch * kChunk; i < i1; ++i) {
+        const double s12 = ev_xy[2 * i], s13 = ev_xy[2 * i + 1];
+        const cplx A = ev.amp(s12, s13);
+        const double A2 = std::norm(A);
+        if (is_data) {
+          if (!(A2 > 0.0) || !std::isfinite(A2)) {
+            cbad[ch] = 1;
+            continue;
+          }
+          s.add(std::log(A2));
+        } else {
+          if (!std::isfinite(A2)) {
+            cbad[ch] = 1;
+            continue;
+          }
+          s.add(A2);
+        }
+        if (want_grad) {
+          ev.amp2_grad(s12, s13, A, g.data());
+          const double w = is_data ? 1.0 / A2 : 1.0;
+          for (int k = 0; k < P; ++k) gs[k].add(w * g[k]);
+        }
+      }
+      csum[ch] = s.value();
+      if (want_grad)
+        for (int k = 0; k < P; ++k) cgrad[ch * P + k] = gs[k].value();
+    }
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+      total->add(csum[ch]);
+      if (want_grad)
+        for (int k = 0; k < P; ++k) gtot[k].add(cgrad[ch * P + k]);
+      if (cbad[ch]) *bad = 1;
+    }
+  };
+
+  CSum sum_log, sum_norm;
+  std::vector<CSum> g_data(P), g_norm(P);
+  int bad = 0;
+  run(n_data, data, true, &sum_log, g_data.data(), &bad);
+  run(n_norm, norm, false, &sum_norm, g_norm.data(), &bad);
+  const double S = sum_norm.value();
+  if (bad || !(S > 0.0)) return ORACLE_ENONPOS;
+  const double I = S / (double)n_norm;
+  *nll = -2.0 * sum_log.value() + 2.0 * (double)n_data * std::log(I);
+  if (want_grad)
+    for (int k = 0; k < P; ++k)
+      grad[k] = -2.0 * g_data[k].value() + 2.0 * (double)n_data * g_norm[k].value() / S;
+  return ORACLE_OK;
+}
+
+int oracle_nll(const oracle_model* md, const double* params, int64_t n_data,
+               const double* data, int64_t n_norm, const double* norm, double* nll,
+               int nthreads) {
+  return oracle_nll_grad(md, params, n_data, data, n_norm, norm, nll, nullptr, nthreads);
+}
+
+}  // extern "C"
