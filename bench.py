@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Throughput of the MIPWA likelihood hot path on one GB300 (or N replicas).
+
+One step = one NLL + gradient evaluation (kinematics, Breit-Wigner terms,
+spline setup and evaluation, Bose-symmetrised |A|^2, log, normalisation sum,
+-2 ln L, adjoint gradient) over the whole workload:
+
+  D+ -> pi- pi+ pi+, rho(770) P-wave + f2(1270) D-wave + 40-knot MIPWA S-wave,
+  10^8 accept-reject data events + 10^8 uniform normalisation events stored as
+  float32 (s12, s13), FP32-mixed arithmetic (FP64 spline solve and accumulators).
+
+The same events are also timed in the plain FP64 form ("fp64_plain"), end to
+end from pinned host buffers ("e2e"), and the FP64 oracle on the host cores
+("cpu_baseline"). ``--impl reference`` times the oracle alone.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/s per NLL+grad eval (FP32-mixed vs FP64 plain, same GB300); % roofline"
+WORKLOAD = ("pipipi_n40_1e8_f32: D+->pi-pi+pi+, rho(770) P + f2(1270) D + 40-knot spline "
+            "S-wave, 1e8 accept-reject data + 1e8 uniform normalisation events, float32 "
+            "(s12,s13)")
+
+# Algorithmic work per event of one NLL+gradient evaluation of this model
+# (2 resonances, one P- and one D-wave; counts in the design doc: add/sub/mul = 1,
+# fused multiply-add = 2, each division, square root, sine/cosine and log = 1).
+FLOPS_PER_EVENT_FWD = 211
+FLOPS_PER_EVENT_GRAD = 291
+# Peaks from unit counts and the maximum SM clock (2070 MHz, 152 SMs):
+#   FP32: 128 lanes x 2 flop x 152 x 2.07 GHz;  FP64: 1.25 TFLOP/s (GB300 nominal).
+PEAK_FP32_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+# DRAM bytes (read + write) per launch of the fused FP32 NLL+gradient kernel
+# from one ncu capture (profiles/eval_kernel_f32_grad.txt), scaled to this
+# workload by events processed; None until captured for the current kernel.
+TRAFFIC_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-events", type=int, default=100_000_000,
+                    help="data events (= normalisation events)")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------- distributed
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(spec, n: int, seed: int):
+    """Data and normalisation samples drawn with the oracle's own density."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    o = oracle.Oracle(spec)
+    truth = synth.true_params(spec)
+    data = synth.accept_reject(spec, n, synth.numpy_density(lambda x: o.density(truth, x)),
+                               seed=seed, dtype=torch.float32).numpy().astype(np.float64)
+    norm = synth.uniform_in_plot(spec, n, synth.numpy_density(
+        lambda x: o.inside(x).astype(np.float64)), seed=seed + 1,
+        dtype=torch.float32).numpy().astype(np.float64)
+    return o, data, norm
+
+
+def cpu_baseline(spec, params, n: int = 200_000, target_s: float = 10.0):
+    """The oracle, as it stands, on a bounded sample: repeated NLL+grad
+    evaluations of n + n events for about target_s seconds."""
+    o, data, norm = oracle_sample(spec, n, seed=101)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o.nll_grad(params, data, norm, threads=cores)
+    once = time.perf_counter() - t0
+    reps = max(1, min(50, int(target_s / max(once, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        o.nll_grad(params, data, norm, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": reps * 2 * n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} data + {n} normalisation events of the same model (float32-rounded, "
+                      f"drawn with the oracle's density), {reps} NLL+grad evaluation(s), "
+                      f"{cores} OpenMP threads"}
+
+
+def run_reference(args, world, rank):
+    import synth
+    if rank != 0:
+        return
+    spec = synth.pipipi(40)
+    params = synth.perturbed_params(spec, 3)
+    n = 100_000
+    o, data, norm = oracle_sample(spec, n, seed=101)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        o.nll_grad(params, data, norm, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.nll_grad(params, data, norm, threads=cores)
+    dt = time.perf_counter() - t0
+    value = args.steps * 2 * n / dt
+    sample = (f"each step: {n} data + {n} normalisation events of the workload's model, "
+              f"FP64 oracle NLL+grad on {cores} host threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        run(args, world, rank, local, stream)
+
+
+def run(args, world, rank, local, stream):
+    import torch
+
+    import synth
+    from paper_1703_03284_gb300 import F32, F64, Likelihood
+
+    spec = synth.pipipi(40)
+    truth = synth.true_params(spec)
+    params = synth.perturbed_params(spec, 3)
+    n = args.n_events
+
+    lik = Likelihood(local, F32)  # follows torch's current stream (`stream`)
+    lik.set_spec(spec)
+    # toy data from the model's own |A|^2 (accept-reject), uniform normalisation
+    data = synth.accept_reject(spec, n, lambda x: lik.amp2(truth, x), seed=1 + 1000 * rank,
+                               device="cuda", dtype=torch.float32, chunk=1 << 24)
+    norm = synth.uniform_in_plot(spec, n, lambda x: lik.inside(x).to(torch.float64),
+                                 seed=2 + 1000 * rank, device="cuda", dtype=torch.float32,
+                                 chunk=1 << 24)
+    lik.set_events(data)
+    lik.set_norm_sample(norm)
+    events = 2 * n
+
+    # ---- FP32-mixed, inputs resident in HBM
+    for _ in range(args.warmup):
+        lik.nll_grad(params)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = lik.launch_count()
+    lik.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lik.nll_grad(params)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    launches = lik.launch_count() - launches0
+    kms, kn = lik.kernel_time()
+    lik.set_timing(False)
+    value = world * events * args.steps / (t_ms / 1e3)
+    k_s = kms / kn / 1e3
+    achieved = FLOPS_PER_EVENT_GRAD * events / k_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
+                "traffic": TRAFFIC_PER_LAUNCH,
+                "kernel": "eval_kernel<float,float2,grad>",
+                "kernel_ms": kms / kn,
+                "peak_note": "FP32 from unit counts x 2070 MHz (nominal, not measured)"}
+
+    # ---- plain FP64 on the same events
+    fp64 = None
+    if args.fp64_steps > 0:
+        lik.set_compute_mode(F64)
+        lik.nll_grad(params)
+        lik.set_timing(True)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            lik.nll_grad(params)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 = max_over_ranks(f0.elapsed_time(f1), world)
+        kms64, kn64 = lik.kernel_time()
+        lik.set_timing(False)
+        lik.set_compute_mode(F32)
+        ach64 = FLOPS_PER_EVENT_GRAD * events / (kms64 / kn64 / 1e3) / 1e12
+        fp64 = {"value": world * events * args.fp64_steps / (t64 / 1e3), "unit": "events/s",
+                "ms_per_step": t64 / args.fp64_steps, "steps": args.fp64_steps,
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": PEAK_FP64_TFLOPS,
+                             "unit": "TFLOP/s", "frac": ach64 / PEAK_FP64_TFLOPS,
+                             "traffic": None, "kernel": "eval_kernel<double,float2,grad>",
+                             "peak_note": "GB300 nominal FP64, not measured"}}
+
+    # ---- end to end from pinned host buffers through the C ABI
+    e2e = None
+    if args.e2e_steps > 0:
+        data_h = data.cpu().pin_memory()
+        norm_h = norm.cpu().pin_memory()
+        lik.set_events(data_h)
+        lik.set_norm_sample(norm_h)
+        lik.nll_grad(params)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.e2e_steps):
+            lik.set_events(data_h)
+            lik.set_norm_sample(norm_h)
+            lik.nll_grad(params)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        te = max_over_ranks(g0.elapsed_time(g1), world)
+        P = spec.n_params
+        e2e = {"value": world * events * args.e2e_steps / (te / 1e3), "unit": "events/s",
+               "ms_per_step": te / args.e2e_steps,
+               "h2d_bytes_per_step": int(data_h.numel() * 4 + norm_h.numel() * 4 + 8 * P),
+               "d2h_bytes_per_step": int(8 * (1 + P) + 4 + 2 * 8)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, params)
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_data": n, "n_norm": n,
+                       "l2": "inputs (1.6 GB) larger than L2 (129 MB); no flush needed",
+                       "parallelism": f"replicas x{world} (no collective)"},
+            "roofline": roofline, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": launches, "clocks": clk,
+        }), flush=True)
+
+
+if __name__ == "__main__":
+    main()

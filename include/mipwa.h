@@ -1,0 +1,172 @@
+/*
+ * mipwa.h -- C ABI of the GB300 (sm_103a) engine for the MIPWA Dalitz-plot
+ * likelihood of arXiv:1703.03284.
+ *
+ * What it computes (paper Sec. 2, Eq. 1, and Sec. 4):
+ *   For a decay D -> h1 h2 h3 with two identical particles (m3 == m2) and the
+ *   Dalitz variables s12 = m^2(h1 h2), s13 = m^2(h1 h3), the amplitude is
+ *
+ *     A(s12,s13) = sum_r c_r [A_r(s12,s13) + A_r(s13,s12)] + A0(s12) + A0(s13)
+ *
+ *   (Eq. 1, Bose-symmetrised as in Sec. 4). A_r is a spin-L relativistic
+ *   Breit-Wigner with running width, Blatt-Weisskopf barrier factors for the
+ *   resonance (radius r_res, breakup momentum q) and the D meson (radius r_D,
+ *   bachelor momentum p in the resonance rest frame), and Zemach angular
+ *   factor Z_1 = -4pq cos(theta), Z_2 = 16 p^2 q^2 (cos^2(theta) - 1/3)
+ *   (the spin-dependent Breit-Wigner of Sec. 2). A0(s) = a(s) exp(i phi(s)) is
+ *   the MIPWA S-wave of Sec. 2: a(s) and phi(s) are natural cubic splines
+ *   through (s_k, a_k) and (s_k, phi_k) at the N boundary points s_k; outside
+ *   [s_0, s_{N-1}] the end segments' cubics continue.
+ *
+ *   The objective is the unbinned -2 ln L of Sec. 2 / Sec. 4:
+ *
+ *     NLL = -2 sum_i ln|A(x_i)|^2 + 2 N_data ln I,   I = (1/N_norm) sum_j |A(y_j)|^2
+ *
+ *   over the data events x_i and a normalisation sample y_j (the evenly spaced
+ *   grid of Sec. 4, or a uniform phase-space sample). The constant Dalitz-plot
+ *   area factor is left out: it shifts NLL by a constant only.
+ *
+ * Parameter vector (P = 2R + 2N doubles, R resonances, N knots):
+ *   [Re c_0, Im c_0, ..., Re c_{R-1}, Im c_{R-1}, a_0..a_{N-1}, phi_0..phi_{N-1}]
+ *
+ * Event layout: n interleaved pairs (s12, s13), either double (MIPWA_F64) or
+ * float (MIPWA_F32), in GeV^2.
+ *
+ * Ownership: every set_* call copies its inputs into memory the context owns;
+ * the caller may free its buffers as soon as the call returns. A host pointer
+ * may be pageable or pinned; a device pointer must belong to the context's
+ * device. Output pointers of the compute calls are host pointers unless the
+ * name says otherwise.
+ *
+ * Errors: every call returns a mipwa_status; on failure mipwa_last_error()
+ * gives a one-line reason. A failed set_* call leaves the previous state of
+ * that item unchanged. Calls on one context must not overlap (one context per
+ * host thread); contexts are independent. All work is queued on the context's
+ * stream; synchronous calls wait for it before returning.
+ */
+#ifndef MIPWA_H
+#define MIPWA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mipwa_ctx mipwa_ctx;
+
+/* One Breit-Wigner term of Eq. 1: pole mass and width in GeV, spin L in {0,1,2}. */
+typedef struct {
+  double mass;
+  double width;
+  int spin;
+} mipwa_resonance;
+
+typedef enum {
+  MIPWA_OK = 0,
+  MIPWA_EINVAL = -1,   /* bad argument: null pointer, size, dtype, unsorted knots ... */
+  MIPWA_EOUTSIDE = -2, /* an event lies outside the Dalitz plot; nothing stored */
+  MIPWA_ENONPOS = -3,  /* |A|^2 <= 0 or non-finite for a data event, or I <= 0 */
+  MIPWA_ECUDA = -4,    /* a CUDA runtime call failed (message in last_error) */
+  MIPWA_ETIMEOUT = -5, /* a bounded device wait gave up */
+  MIPWA_ESTATE = -6,   /* call order: model / events / normalisation not set */
+  MIPWA_ENOMEM = -7    /* device or pinned host allocation failed */
+} mipwa_status;
+
+/* Storage type of event pairs, and compute mode of a context. */
+enum {
+  MIPWA_F64 = 0, /* plain FP64 arithmetic throughout                           */
+  MIPWA_F32 = 1  /* FP32 amplitudes; FP64 spline solve and FP64 accumulators   */
+};
+
+/* Limits of one context. */
+#define MIPWA_MAX_RES 4
+#define MIPWA_MAX_KNOTS 64
+
+/* Create a context on CUDA device `device` computing in `compute_mode`
+ * (MIPWA_F64 or MIPWA_F32). The context owns a non-blocking CUDA stream until
+ * mipwa_set_stream() replaces it. On failure *out is NULL. */
+int mipwa_create(mipwa_ctx** out, int device, int compute_mode);
+
+/* Release every device and host buffer of the context. NULL is a no-op. */
+void mipwa_destroy(mipwa_ctx* ctx);
+
+/* Queue all further work on `stream`, a cudaStream_t of the context's device
+ * (e.g. torch.cuda.current_stream().cuda_stream; NULL is the legacy default
+ * stream, as everywhere in CUDA). Work already queued on the previous stream
+ * is waited for first. The caller keeps ownership of `stream`; the context's
+ * own stream is used until the first call. */
+int mipwa_set_stream(mipwa_ctx* ctx, void* stream);
+
+/* Switch between MIPWA_F64 and MIPWA_F32 arithmetic; stored events are kept. */
+int mipwa_set_compute_mode(mipwa_ctx* ctx, int compute_mode);
+
+/* Masses in GeV of the decaying meson, the odd particle h1 and the two
+ * identical particles h2 = h3 (Sec. 2: D -> R h3, R -> h1 h2). Requires
+ * mD > m1 + 2 m2 and m1, m2 >= 0. Clears the model and any stored samples. */
+int mipwa_set_masses(mipwa_ctx* ctx, double mD, double m1, double m2);
+
+/* The amplitude model of Eq. 1: n_res Breit-Wigner terms (0..MIPWA_MAX_RES,
+ * each mass > m1 + m2, width > 0, spin 0..2), the n_knots (2..MIPWA_MAX_KNOTS)
+ * strictly increasing S-wave boundary points s_k in GeV^2 (Sec. 2), and the
+ * Blatt-Weisskopf radii in 1/GeV. Needs set_masses first. Fixes P = 2 n_res +
+ * 2 n_knots. Stored events stay valid. */
+int mipwa_set_model(mipwa_ctx* ctx, const mipwa_resonance* res, int n_res,
+                    const double* knots, int n_knots, double r_res, double r_D);
+
+/* Data events x_i: n pairs (s12, s13) of type `dtype` at `s12s13` (a device
+ * pointer when on_device != 0). n may be 0. Every event must lie inside the
+ * Dalitz plot; otherwise the call stores nothing, writes the number of
+ * outside events to *n_outside (if not NULL) and returns MIPWA_EOUTSIDE.
+ * Needs set_masses first. */
+int mipwa_set_events(mipwa_ctx* ctx, const void* s12s13, int64_t n, int dtype,
+                     int on_device, int64_t* n_outside);
+
+/* Normalisation sample y_j (Sec. 4: evenly spaced grid points or a uniform
+ * phase-space sample), same conventions as mipwa_set_events; n >= 1. */
+int mipwa_set_norm_sample(mipwa_ctx* ctx, const void* s12s13, int64_t n, int dtype,
+                          int on_device, int64_t* n_outside);
+
+/* P = 2 n_res + 2 n_knots of the current model, or -1 without a model. */
+int mipwa_num_params(const mipwa_ctx* ctx);
+
+/* NLL at `params` (P host doubles) into *nll. Blocks until done. */
+int mipwa_nll(mipwa_ctx* ctx, const double* params, double* nll);
+
+/* NLL and its gradient d NLL / d params (P host doubles) at `params`, by the
+ * adjoint of the per-event amplitude (amplitudes recomputed, nothing stored
+ * per event). Blocks until done. */
+int mipwa_nll_grad(mipwa_ctx* ctx, const double* params, double* nll, double* grad);
+
+/* |A(s12,s13)|^2 at `params` for n events at the DEVICE pointer `d_s12s13`
+ * (type dtype), written as doubles to the DEVICE pointer `d_out`; events
+ * outside the Dalitz plot get 0 (the PDF has no support there). Computed in
+ * the context's compute mode. Blocks until done. */
+int mipwa_amp2(mipwa_ctx* ctx, const double* params, const void* d_s12s13, int64_t n,
+               int dtype, double* d_out);
+
+/* d_out[i] = 1 if event i at the DEVICE pointer d_s12s13 lies inside the
+ * Dalitz plot, else 0 (FP64 boundary test). Needs set_masses. Blocks. */
+int mipwa_inside(mipwa_ctx* ctx, const void* d_s12s13, int64_t n, int dtype,
+                 uint8_t* d_out);
+
+/* Kernel timing (diagnostics, off by default): while on, each evaluation
+ * records CUDA events on the context's stream around its fused event kernel;
+ * mipwa_kernel_time() returns the summed kernel milliseconds and the number of
+ * timed launches since timing was last switched on. */
+int mipwa_set_timing(mipwa_ctx* ctx, int on);
+int mipwa_kernel_time(mipwa_ctx* ctx, double* ms, int64_t* n_launches);
+
+/* One-line description of the last failure on this context ("" if none). */
+const char* mipwa_last_error(const mipwa_ctx* ctx);
+
+/* Number of kernel launches this context has queued since creation
+ * (diagnostics and benchmark bookkeeping). */
+int64_t mipwa_launch_count(const mipwa_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MIPWA_H */

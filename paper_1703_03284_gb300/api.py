@@ -1,0 +1,209 @@
+"""Python binding of the MIPWA likelihood engine: one class whose methods carry
+the names of the C entry points (include/mipwa.h) and only marshal arguments.
+
+Events may be numpy arrays or torch tensors of shape (n, 2) holding (s12, s13)
+in float64 or float32; CUDA tensors are passed to the library as device
+pointers, everything else as host pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import F32, F64
+
+
+class MipwaError(RuntimeError):
+    def __init__(self, status: int, message: str, n_outside: int = 0):
+        self.status = status
+        self.n_outside = n_outside
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {message}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _event_buffer(x):
+    """Return (pointer, n, dtype code, on_device, keepalive) for an (n, 2) array."""
+    try:
+        torch = _torch()
+        is_tensor = isinstance(x, torch.Tensor)
+    except ImportError:  # pragma: no cover - torch is part of the runtime
+        is_tensor = False
+    if is_tensor:
+        if x.dim() != 2 or x.shape[1] != 2:
+            raise ValueError("events must have shape (n, 2)")
+        if x.dtype not in (torch.float32, torch.float64):
+            raise ValueError("events must be float32 or float64")
+        t = x.contiguous()
+        code = F32 if t.dtype == torch.float32 else F64
+        return t.data_ptr(), t.shape[0], code, int(t.is_cuda), t
+    a = np.asarray(x)
+    if a.ndim != 2 or a.shape[1] != 2:
+        raise ValueError("events must have shape (n, 2)")
+    if a.dtype not in (np.float32, np.float64):
+        a = a.astype(np.float64)
+    a = np.ascontiguousarray(a)
+    code = F32 if a.dtype == np.float32 else F64
+    return a.ctypes.data, a.shape[0], code, 0, a
+
+
+class Likelihood:
+    """One library context (``mipwa_ctx``) on one CUDA device."""
+
+    def __init__(self, device: int = 0, compute_mode: int = F64):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        rc = self._lib.mipwa_create(ctypes.byref(h), int(device), int(compute_mode))
+        if rc != _lib.OK:
+            raise MipwaError(rc, f"mipwa_create(device={device}) failed")
+        self._h = h
+        self.device = device
+        self.n_params = -1
+        self.follow_torch_stream = True
+        self._stream = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.mipwa_destroy(h)
+            self._h = None
+
+    def _follow_stream(self):
+        """Queue the library's work on torch's current stream of this device, so
+        that it is ordered with the torch work that made or reads its tensors."""
+        torch = _torch()
+        if self.follow_torch_stream and torch.cuda.is_available():
+            s = torch.cuda.current_stream(self.device).cuda_stream
+            if s != self._stream:
+                self._check(self._lib.mipwa_set_stream(self._h, ctypes.c_void_p(s)))
+                self._stream = s
+
+    def _check(self, rc: int, n_outside: int = 0):
+        if rc != _lib.OK:
+            raise MipwaError(rc, self.last_error(), n_outside)
+
+    # ---------------------------------------------------------------- setup
+    def set_stream(self, stream):
+        """Queue work on a torch.cuda.Stream or raw cudaStream_t handle and stop
+        following torch's current stream."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        self.follow_torch_stream = False
+        self._check(self._lib.mipwa_set_stream(self._h, ctypes.c_void_p(ptr)))
+        self._stream = ptr
+
+    def set_compute_mode(self, mode: int):
+        self._check(self._lib.mipwa_set_compute_mode(self._h, int(mode)))
+
+    def set_masses(self, mD: float, m1: float, m2: float):
+        self._check(self._lib.mipwa_set_masses(self._h, mD, m1, m2))
+
+    def set_model(self, resonances: Sequence, knots: Sequence[float], r_res: float, r_D: float):
+        res = (_lib.Resonance * max(len(resonances), 1))()
+        for i, (mass, width, spin) in enumerate(resonances):
+            res[i] = _lib.Resonance(float(mass), float(width), int(spin))
+        kn = np.ascontiguousarray(knots, dtype=np.float64)
+        self._check(self._lib.mipwa_set_model(
+            self._h, res, len(resonances), kn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            len(kn), float(r_res), float(r_D)))
+        self.n_params = self.num_params()
+
+    def set_spec(self, spec):
+        """set_masses + set_model from an object with mD, m1, m2, resonances,
+        knots, r_res, r_D attributes."""
+        self.set_masses(spec.mD, spec.m1, spec.m2)
+        self.set_model(spec.resonances, spec.knots, spec.r_res, spec.r_D)
+
+    def _set(self, fn, x):
+        self._follow_stream()
+        ptr, n, code, on_dev, keep = _event_buffer(x)
+        n_out = ctypes.c_int64(0)
+        rc = fn(self._h, ctypes.c_void_p(ptr), n, code, on_dev, ctypes.byref(n_out))
+        del keep
+        self._check(rc, n_out.value)
+
+    def set_events(self, x):
+        self._set(self._lib.mipwa_set_events, x)
+
+    def set_norm_sample(self, x):
+        self._set(self._lib.mipwa_set_norm_sample, x)
+
+    def num_params(self) -> int:
+        return int(self._lib.mipwa_num_params(self._h))
+
+    # -------------------------------------------------------------- compute
+    def _params(self, params) -> np.ndarray:
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1))
+        if p.shape[0] != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {p.shape[0]}")
+        return p
+
+    def nll(self, params) -> float:
+        self._follow_stream()
+        p = self._params(params)
+        out = ctypes.c_double()
+        self._check(self._lib.mipwa_nll(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.byref(out)))
+        return out.value
+
+    def nll_grad(self, params):
+        self._follow_stream()
+        p = self._params(params)
+        out = ctypes.c_double()
+        g = np.empty_like(p)
+        self._check(self._lib.mipwa_nll_grad(
+            self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(out),
+            g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out.value, g
+
+    def amp2(self, params, events):
+        """|A|^2 per event (0 outside the Dalitz plot) for a CUDA tensor of events;
+        returns a float64 CUDA tensor."""
+        torch = _torch()
+        if not (isinstance(events, torch.Tensor) and events.is_cuda):
+            raise ValueError("amp2 takes a CUDA tensor of events")
+        self._follow_stream()
+        ptr, n, code, _, keep = _event_buffer(events)
+        out = torch.empty(n, dtype=torch.float64, device=events.device)
+        p = self._params(params)
+        self._check(self._lib.mipwa_amp2(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.c_void_p(ptr), n, code,
+                                         ctypes.c_void_p(out.data_ptr())))
+        del keep
+        return out
+
+    def inside(self, events):
+        """Boolean CUDA tensor: event inside the Dalitz plot."""
+        torch = _torch()
+        if not (isinstance(events, torch.Tensor) and events.is_cuda):
+            raise ValueError("inside takes a CUDA tensor of events")
+        self._follow_stream()
+        ptr, n, code, _, keep = _event_buffer(events)
+        out = torch.empty(n, dtype=torch.uint8, device=events.device)
+        self._check(self._lib.mipwa_inside(self._h, ctypes.c_void_p(ptr), n, code,
+                                           ctypes.c_void_p(out.data_ptr())))
+        del keep
+        return out.bool()
+
+    # ----------------------------------------------------------- diagnostics
+    def set_timing(self, on: bool = True):
+        self._check(self._lib.mipwa_set_timing(self._h, int(bool(on))))
+
+    def kernel_time(self):
+        """(summed milliseconds, launches) of the fused event kernel since timing was on."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self._lib.mipwa_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def last_error(self) -> str:
+        s = self._lib.mipwa_last_error(self._h)
+        return s.decode() if s else ""
+
+    def launch_count(self) -> int:
+        return int(self._lib.mipwa_launch_count(self._h))

@@ -1,0 +1,545 @@
+// C ABI of the MIPWA likelihood engine: context, validation, device memory and
+// the launch sequence of one evaluation (see include/mipwa.h for the contract).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/mipwa.h"
+#include "mipwa_kernels.cuh"
+
+using namespace mipwa;
+
+struct mipwa_ctx {
+  int device = 0;
+  int mode = MIPWA_F64;
+  int sm_count = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  bool have_masses = false, have_model = false;
+  Model model{};
+  int n_params = -1;
+  std::vector<double> lu_host;
+  // device buffers
+  double* d_lu = nullptr;
+  double* d_params = nullptr;
+  double* d_coef = nullptr;
+  double* d_out = nullptr;
+  int* d_flags = nullptr;
+  unsigned int* d_counter = nullptr;
+  unsigned long long* d_count = nullptr;
+  double* d_partials = nullptr;
+  size_t partials_cap = 0;  // doubles
+  double* h_stage = nullptr;  // pinned: params in, results out
+  // samples (double-buffered so that a rejected set_* keeps the old one)
+  struct Sample {
+    void* cur = nullptr;
+    size_t cur_cap = 0;
+    void* spare = nullptr;
+    size_t spare_cap = 0;
+    int64_t n = 0;
+    int dtype = MIPWA_F64;
+    bool set = false;
+  } data, norm;
+  int64_t launches = 0;
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double kernel_ms = 0.0;
+  int64_t kernel_n = 0;
+  char err[512] = {0};
+};
+
+namespace {
+
+constexpr int kStage = 2 * (2 * kMaxRes + 2 * kMaxKnots + 8);
+
+int fail(mipwa_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(ctx, call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? MIPWA_ENOMEM : MIPWA_ECUDA, \
+                  "%s: %s", #call, cudaGetErrorString(e_));                            \
+  } while (0)
+
+size_t ev_bytes(int dtype) { return dtype == MIPWA_F32 ? 2 * sizeof(float) : 2 * sizeof(double); }
+
+void split(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+double kallen_sqrt(double x, double a, double b) {
+  const double l = (x - (a + b) * (a + b)) * (x - (a - b) * (a - b));
+  return std::sqrt(l);
+}
+
+// Fill the double and float constant blocks from masses, resonances and radii.
+void derive(Model& m, const mipwa_resonance* res, int n_res, double r_res, double r_D) {
+  const double M = m.mD, m1 = m.m1, m2 = m.m2, m3 = m.m2;
+  Consts<double>& d = m.cd;
+  Consts<float>& f = m.cf;
+  d.thr_p = (m1 + m2) * (m1 + m2);
+  d.thr_m = (m1 - m2) * (m1 - m2);
+  d.pthr_p = (M + m3) * (M + m3);
+  d.pthr_m = (M - m3) * (M - m3);
+  d.sigma = M * M + m1 * m1 + m2 * m2 + m3 * m3;
+  d.zc1 = (M * M - m3 * m3) * (m2 * m2 - m1 * m1);
+  d.r2_res = r_res * r_res;
+  d.r2_D = r_D * r_D;
+  d.thr_p_lo = d.thr_m_lo = d.pthr_p_lo = d.pthr_m_lo = d.sigma_lo = 0.0;
+  for (int r = 0; r < kMaxRes; ++r) {
+    d.m2[r] = d.m2_lo[r] = d.g[r] = d.nR[r] = d.nD[r] = 0.0;
+    d.L[r] = 0;
+  }
+  m.n_res = n_res;
+  for (int r = 0; r < n_res; ++r) {
+    const double mr = res[r].mass, G = res[r].width;
+    const int L = res[r].spin;
+    const double q0 = kallen_sqrt(mr * mr, m1, m2) / (2.0 * mr);
+    const double p0 = kallen_sqrt(mr * mr, M, m3) / (2.0 * mr);
+    const double z0R = d.r2_res * q0 * q0, z0D = d.r2_D * p0 * p0;
+    d.m2[r] = mr * mr;
+    d.L[r] = L;
+    d.g[r] = mr * mr * G / std::pow(q0, 2 * L + 1);
+    d.nR[r] = L == 1 ? 1.0 + z0R : (L == 2 ? z0R * z0R + 3.0 * z0R + 9.0 : 1.0);
+    d.nD[r] = L == 1 ? 1.0 + z0D : (L == 2 ? z0D * z0D + 3.0 * z0D + 9.0 : 1.0);
+  }
+  split(d.thr_p, f.thr_p, f.thr_p_lo);
+  split(d.thr_m, f.thr_m, f.thr_m_lo);
+  split(d.pthr_p, f.pthr_p, f.pthr_p_lo);
+  split(d.pthr_m, f.pthr_m, f.pthr_m_lo);
+  split(d.sigma, f.sigma, f.sigma_lo);
+  f.zc1 = (float)d.zc1;
+  f.r2_res = (float)d.r2_res;
+  f.r2_D = (float)d.r2_D;
+  for (int r = 0; r < kMaxRes; ++r) {
+    split(d.m2[r], f.m2[r], f.m2_lo[r]);
+    f.g[r] = (float)d.g[r];
+    f.nR[r] = (float)d.nR[r];
+    f.nD[r] = (float)d.nD[r];
+    f.L[r] = d.L[r];
+  }
+}
+
+// Eliminate the natural-spline tridiagonal system of the knots once (Thomas).
+void factor_spline(const Knots& kn, std::vector<double>& lu) {
+  const int N = kn.n, nseg = N - 1, mm = N - 2;
+  lu.assign(SplineLU::size(N), 0.0);
+  double* h = lu.data();
+  double* ih = h + nseg;
+  double* w = ih + nseg;
+  double* idia = w + (mm > 0 ? mm : 0);
+  double* sup = idia + (mm > 0 ? mm : 0);
+  for (int j = 0; j < nseg; ++j) {
+    h[j] = kn.s[j + 1] - kn.s[j];
+    ih[j] = 1.0 / h[j];
+  }
+  double prev_dia = 0.0;
+  for (int i = 0; i < mm; ++i) {
+    const int k = i + 1;
+    const double sub = h[k - 1] / 6.0, dia = (h[k - 1] + h[k]) / 3.0;
+    sup[i] = h[k] / 6.0;
+    double dd = dia;
+    if (i > 0) {
+      w[i] = sub / prev_dia;
+      dd = dia - w[i] * sup[i - 1];
+    }
+    idia[i] = 1.0 / dd;
+    prev_dia = dd;
+  }
+}
+
+int ensure(mipwa_ctx* c, void** p, size_t* cap, size_t bytes) {
+  if (*cap >= bytes && *p) return MIPWA_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (bytes == 0) return MIPWA_OK;
+  CK(c, cudaMalloc(p, bytes));
+  *cap = bytes;
+  return MIPWA_OK;
+}
+
+int check_ctx(mipwa_ctx* c) {
+  if (!c) return MIPWA_EINVAL;
+  c->err[0] = 0;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return fail(c, MIPWA_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  return MIPWA_OK;
+}
+
+// Non-zero when p is device (or managed) memory the kernels may dereference.
+int is_device_ptr(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+int grid_for(mipwa_ctx* c, int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)c->sm_count * 8;
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : (int)g;
+}
+
+int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n, int dtype,
+               int on_device, int64_t* n_outside, bool allow_empty) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (n_outside) *n_outside = 0;
+  if (!c->have_masses) return fail(c, MIPWA_ESTATE, "set_masses must come first");
+  if (dtype != MIPWA_F32 && dtype != MIPWA_F64) return fail(c, MIPWA_EINVAL, "bad dtype %d", dtype);
+  if (n < 0 || (n == 0 && !allow_empty)) return fail(c, MIPWA_EINVAL, "bad event count %lld", (long long)n);
+  if (n > 0 && !ptr) return fail(c, MIPWA_EINVAL, "null event pointer");
+  const size_t bytes = (size_t)n * ev_bytes(dtype);
+  rc = ensure(c, &smp.spare, &smp.spare_cap, bytes);
+  if (rc) return rc;
+  unsigned long long outside = 0;
+  if (n > 0) {
+    if (on_device) {
+      if (!is_device_ptr(ptr))
+        return fail(c, MIPWA_EINVAL, "on_device set but the pointer is not device memory");
+      CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream));
+    CK(c, launch_inside(dtype == MIPWA_F32, c->model, smp.spare, n, nullptr, c->d_count,
+                        grid_for(c, n), c->stream));
+    c->launches++;
+    CK(c, cudaMemcpyAsync(&outside, c->d_count, sizeof(outside), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  if (outside > 0) {
+    if (n_outside) *n_outside = (int64_t)outside;
+    return fail(c, MIPWA_EOUTSIDE, "%llu of %lld events lie outside the Dalitz plot", outside,
+                (long long)n);
+  }
+  std::swap(smp.cur, smp.spare);
+  std::swap(smp.cur_cap, smp.spare_cap);
+  smp.n = n;
+  smp.dtype = dtype;
+  smp.set = true;
+  return MIPWA_OK;
+}
+
+int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool want_grad) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!params || !nll || (want_grad && !grad)) return fail(c, MIPWA_EINVAL, "null pointer");
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  if (!c->data.set) return fail(c, MIPWA_ESTATE, "set_events must come first");
+  if (!c->norm.set) return fail(c, MIPWA_ESTATE, "set_norm_sample must come first");
+  if (c->data.n > 0 && c->data.dtype != c->norm.dtype)
+    return fail(c, MIPWA_EINVAL, "data and normalisation samples must share a dtype");
+  const int P = c->n_params;
+  for (int k = 0; k < P; ++k)
+    if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
+  const int f32 = c->mode == MIPWA_F32;
+  const int ev32 = c->norm.dtype == MIPWA_F32;
+  const int per_sm = eval_blocks_per_sm(f32, ev32, want_grad);
+  int total = c->sm_count * per_sm;
+  const int64_t need_d = (c->data.n + kThreads - 1) / kThreads;
+  const int64_t need_n = (c->norm.n + kThreads - 1) / kThreads;
+  int nb_d = 0;
+  if (c->data.n > 0) {
+    const double frac = (double)c->data.n / (double)(c->data.n + c->norm.n);
+    nb_d = (int)std::lround(total * frac);
+    if (nb_d < 1) nb_d = 1;
+    if (nb_d > total - 1) nb_d = total - 1;
+    if (nb_d > need_d) nb_d = (int)need_d;
+  }
+  int nb_n = total - nb_d;
+  if (nb_n > need_n) nb_n = (int)need_n;
+  if (nb_n < 1) nb_n = 1;
+  const int grid = nb_d + nb_n;
+  const int W = partial_width(c->model.kn.n, c->model.n_res, want_grad);
+  rc = ensure(c, (void**)&c->d_partials, &c->partials_cap, (size_t)grid * W * sizeof(double));
+  if (rc) return rc;
+
+  std::memcpy(c->h_stage, params, P * sizeof(double));
+  CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, P * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
+  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->stream);
+  CK(c, cudaGetLastError());
+  EvalArgs a;
+  a.data = c->data.cur;
+  a.norm = c->norm.cur;
+  a.n_data = c->data.n;
+  a.n_norm = c->norm.n;
+  a.nb_data = nb_d;
+  a.nb_norm = nb_n;
+  a.n_params = P;
+  a.coef = c->d_coef;
+  a.lu = c->d_lu;
+  a.partials = c->d_partials;
+  a.counter = c->d_counter;
+  a.out = c->d_out;
+  a.flags = c->d_flags;
+  a.model = c->model;
+  if (c->timing) CK(c, cudaEventRecord(c->ev0, c->stream));
+  CK(c, launch_eval(f32, ev32, want_grad, a, grid, c->stream));
+  if (c->timing) CK(c, cudaEventRecord(c->ev1, c->stream));
+  c->launches += 2;
+  double* h_out = c->h_stage + kStage / 2;
+  int* h_flags = (int*)(h_out + 1 + P);
+  CK(c, cudaMemcpyAsync(h_out, c->d_out, (1 + (want_grad ? P : 0)) * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(h_flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (c->timing) {
+    float ms = 0.0f;
+    CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    c->kernel_ms += ms;
+    c->kernel_n++;
+  }
+  if (*h_flags & kFlagData)
+    return fail(c, MIPWA_ENONPOS, "|A|^2 <= 0 or non-finite for a data event");
+  if (*h_flags & (kFlagNorm | kFlagIntegral) || !std::isfinite(h_out[0]))
+    return fail(c, MIPWA_ENONPOS, "normalisation integral is not positive and finite");
+  *nll = h_out[0];
+  if (want_grad) std::memcpy(grad, h_out + 1, P * sizeof(double));
+  return MIPWA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
+  if (!out) return MIPWA_EINVAL;
+  *out = nullptr;
+  if (compute_mode != MIPWA_F64 && compute_mode != MIPWA_F32) return MIPWA_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MIPWA_ECUDA;
+  }
+  mipwa_ctx* c = new mipwa_ctx();
+  c->device = device;
+  c->mode = compute_mode;
+  auto bail = [&](int code) {
+    mipwa_destroy(c);
+    return code;
+  };
+  if (cudaSetDevice(device) != cudaSuccess) return bail(MIPWA_ECUDA);
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return bail(MIPWA_ECUDA);
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(MIPWA_ECUDA);
+  c->stream = c->own_stream;
+  const int P = 2 * kMaxRes + 2 * kMaxKnots;
+  if (cudaMalloc(&c->d_lu, SplineLU::size(kMaxKnots) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_params, P * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_coef, coef_size(kMaxKnots, kMaxRes) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_out, (1 + P) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_counter, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&c->h_stage, kStage * sizeof(double)) != cudaSuccess)
+    return bail(MIPWA_ENOMEM);
+  if (cudaMemset(c->d_counter, 0, sizeof(unsigned int)) != cudaSuccess) return bail(MIPWA_ECUDA);
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
+    return bail(MIPWA_ECUDA);
+  *out = c;
+  return MIPWA_OK;
+}
+
+void mipwa_destroy(mipwa_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : {(void*)c->d_lu, (void*)c->d_params, (void*)c->d_coef, (void*)c->d_out,
+                  (void*)c->d_flags, (void*)c->d_counter, (void*)c->d_count,
+                  (void*)c->d_partials, c->data.cur, c->data.spare, c->norm.cur,
+                  c->norm.spare})
+    if (p) cudaFree(p);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+int mipwa_set_stream(mipwa_ctx* c, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((cudaStream_t)stream == c->stream) return MIPWA_OK;
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->stream = (cudaStream_t)stream;
+  return MIPWA_OK;
+}
+
+int mipwa_set_compute_mode(mipwa_ctx* c, int mode) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (mode != MIPWA_F64 && mode != MIPWA_F32) return fail(c, MIPWA_EINVAL, "bad compute mode");
+  c->mode = mode;
+  return MIPWA_OK;
+}
+
+int mipwa_set_masses(mipwa_ctx* c, double mD, double m1, double m2) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!(std::isfinite(mD) && std::isfinite(m1) && std::isfinite(m2)) || m1 < 0 || m2 < 0 ||
+      !(mD > m1 + 2.0 * m2))
+    return fail(c, MIPWA_EINVAL, "masses must satisfy mD > m1 + 2 m2, m1, m2 >= 0");
+  c->model.mD = mD;
+  c->model.m1 = m1;
+  c->model.m2 = m2;
+  c->have_masses = true;
+  c->have_model = false;
+  c->n_params = -1;
+  c->data.set = c->norm.set = false;
+  c->data.n = c->norm.n = 0;
+  return MIPWA_OK;
+}
+
+int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const double* knots,
+                    int n_knots, double r_res, double r_D) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_masses) return fail(c, MIPWA_ESTATE, "set_masses must come first");
+  if (n_res < 0 || n_res > kMaxRes || (n_res > 0 && !res))
+    return fail(c, MIPWA_EINVAL, "n_res must be in 0..%d", kMaxRes);
+  if (n_knots < 2 || n_knots > kMaxKnots || !knots)
+    return fail(c, MIPWA_EINVAL, "n_knots must be in 2..%d", kMaxKnots);
+  if (!(std::isfinite(r_res) && std::isfinite(r_D)) || r_res < 0 || r_D < 0)
+    return fail(c, MIPWA_EINVAL, "radii must be finite and >= 0");
+  const double thr = c->model.m1 + c->model.m2, top = c->model.mD - c->model.m2;
+  for (int r = 0; r < n_res; ++r) {
+    if (!(res[r].mass > thr && res[r].mass < top) || !(res[r].width > 0) ||
+        !std::isfinite(res[r].width) || res[r].spin < 0 || res[r].spin > 2)
+      return fail(c, MIPWA_EINVAL,
+                  "resonance %d: need m1+m2 < mass < mD-m2, width > 0, spin 0..2", r);
+  }
+  for (int k = 0; k < n_knots; ++k) {
+    if (!std::isfinite(knots[k])) return fail(c, MIPWA_EINVAL, "knot %d is not finite", k);
+    if (k > 0 && !(knots[k] > knots[k - 1]))
+      return fail(c, MIPWA_EINVAL, "knots must be strictly increasing");
+  }
+  Model m = c->model;
+  derive(m, res, n_res, r_res, r_D);
+  Knots& kn = m.kn;
+  kn.n = n_knots;
+  for (int k = 0; k < kMaxKnots; ++k) kn.s[k] = k < n_knots ? knots[k] : 0.0;
+  kn.s0 = knots[0];
+  kn.h = (knots[n_knots - 1] - knots[0]) / (n_knots - 1);
+  kn.inv_h = 1.0 / kn.h;
+  kn.uniform = 1;
+  const double scale = std::fabs(knots[0]) + std::fabs(knots[n_knots - 1]);
+  for (int k = 0; k < n_knots; ++k)
+    if (std::fabs(knots[k] - (kn.s0 + k * kn.h)) > 1e-12 * scale) kn.uniform = 0;
+  std::vector<double> lu;
+  factor_spline(kn, lu);
+  CK(c, cudaMemcpyAsync(c->d_lu, lu.data(), lu.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->lu_host = lu;
+  c->model = m;
+  c->n_params = 2 * n_res + 2 * n_knots;
+  c->have_model = true;
+  return MIPWA_OK;
+}
+
+int mipwa_set_events(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, int on_device,
+                     int64_t* n_outside) {
+  if (!c) return MIPWA_EINVAL;
+  return set_sample(c, c->data, ptr, n, dtype, on_device, n_outside, true);
+}
+
+int mipwa_set_norm_sample(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, int on_device,
+                          int64_t* n_outside) {
+  if (!c) return MIPWA_EINVAL;
+  return set_sample(c, c->norm, ptr, n, dtype, on_device, n_outside, false);
+}
+
+int mipwa_num_params(const mipwa_ctx* c) { return (c && c->have_model) ? c->n_params : -1; }
+
+int mipwa_nll(mipwa_ctx* c, const double* params, double* nll) {
+  return evaluate(c, params, nll, nullptr, false);
+}
+
+int mipwa_nll_grad(mipwa_ctx* c, const double* params, double* nll, double* grad) {
+  return evaluate(c, params, nll, grad, true);
+}
+
+int mipwa_amp2(mipwa_ctx* c, const double* params, const void* ev, int64_t n, int dtype,
+               double* out) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  if (!params || n < 0 || (n > 0 && (!ev || !out))) return fail(c, MIPWA_EINVAL, "bad argument");
+  if (dtype != MIPWA_F32 && dtype != MIPWA_F64) return fail(c, MIPWA_EINVAL, "bad dtype");
+  if (n > 0 && (!is_device_ptr(ev) || !is_device_ptr(out)))
+    return fail(c, MIPWA_EINVAL, "amp2 takes device pointers");
+  for (int k = 0; k < c->n_params; ++k)
+    if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
+  if (n == 0) return MIPWA_OK;
+  std::memcpy(c->h_stage, params, c->n_params * sizeof(double));
+  CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, c->n_params * sizeof(double),
+                        cudaMemcpyHostToDevice, c->stream));
+  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->stream);
+  CK(c, cudaGetLastError());
+  CK(c, launch_amp2(c->mode == MIPWA_F32, dtype == MIPWA_F32, c->model, c->d_coef, ev, n, out,
+                    grid_for(c, n), c->stream));
+  c->launches += 2;
+  CK(c, cudaStreamSynchronize(c->stream));
+  return MIPWA_OK;
+}
+
+int mipwa_inside(mipwa_ctx* c, const void* ev, int64_t n, int dtype, uint8_t* out) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_masses) return fail(c, MIPWA_ESTATE, "set_masses must come first");
+  if (n < 0 || (n > 0 && (!ev || !out))) return fail(c, MIPWA_EINVAL, "bad argument");
+  if (dtype != MIPWA_F32 && dtype != MIPWA_F64) return fail(c, MIPWA_EINVAL, "bad dtype");
+  if (n == 0) return MIPWA_OK;
+  if (!is_device_ptr(ev) || !is_device_ptr(out))
+    return fail(c, MIPWA_EINVAL, "inside takes device pointers");
+  CK(c, launch_inside(dtype == MIPWA_F32, c->model, ev, n, out, nullptr, grid_for(c, n),
+                      c->stream));
+  c->launches++;
+  CK(c, cudaStreamSynchronize(c->stream));
+  return MIPWA_OK;
+}
+
+int mipwa_set_timing(mipwa_ctx* c, int on) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->timing = on != 0;
+  c->kernel_ms = 0.0;
+  c->kernel_n = 0;
+  return MIPWA_OK;
+}
+
+int mipwa_kernel_time(mipwa_ctx* c, double* ms, int64_t* n) {
+  if (!c || !ms || !n) return MIPWA_EINVAL;
+  *ms = c->kernel_ms;
+  *n = c->kernel_n;
+  return MIPWA_OK;
+}
+
+const char* mipwa_last_error(const mipwa_ctx* c) { return c ? c->err : "null context"; }
+
+int64_t mipwa_launch_count(const mipwa_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// Per-evaluation spline setup of the MIPWA S-wave (arXiv:1703.03284, Sec. 2:
+// a_k, phi_k at the N boundary points, cubic spline in between).
+//
+// Natural boundary conditions: M_0 = M_{N-1} = 0, and for k = 1..N-2
+//   h_{k-1}/6 M_{k-1} + (h_{k-1}+h_k)/3 M_k + h_k/6 M_{k+1} = (D y)_k,
+//   (D y)_k = (y_{k+1}-y_k)/h_k - (y_k-y_{k-1})/h_{k-1}.
+// The tridiagonal matrix depends on the knots only; it is eliminated once on
+// the host, so each evaluation does two substitutions per spline here, in
+// FP64, then writes each segment's cubic as a polynomial in t = s - s_j:
+//   S = y_j + t [(y_{j+1}-y_j)/h_j - h_j (2 M_j + M_{j+1})/6] + t^2 M_j/2
+//       + t^3 (M_{j+1} - M_j)/(6 h_j).
+#include <cuda_runtime.h>
+
+#include "mipwa_kernels.cuh"
+
+namespace mipwa {
+
+__global__ void prepare_kernel(const int n_res, const int N, const double* __restrict__ params,
+                               const double* __restrict__ lu, double* __restrict__ coef) {
+  __shared__ double M[2][kMaxKnots];
+  const int nseg = N - 1, mm = N - 2;
+  const double* h = lu;
+  const double* ih = lu + nseg;
+  const double* w = lu + 2 * nseg;
+  const double* idia = w + mm;
+  const double* sup = idia + mm;
+  const double* y_all = params + 2 * n_res;
+  const int sp = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 ? 1 : -1);
+  if (sp >= 0) {
+    const double* y = y_all + sp * N;
+    double* Ms = M[sp];
+    Ms[0] = 0.0;
+    Ms[N - 1] = 0.0;
+    if (mm >= 1) {
+      double* v = Ms + 1;  // interior unknowns M_1..M_{N-2}
+      for (int k = 1; k <= mm; ++k)
+        v[k - 1] = (y[k + 1] - y[k]) * ih[k] - (y[k] - y[k - 1]) * ih[k - 1];
+      for (int i = 1; i < mm; ++i) v[i] -= w[i] * v[i - 1];
+      v[mm - 1] *= idia[mm - 1];
+      for (int i = mm - 2; i >= 0; --i) v[i] = (v[i] - sup[i] * v[i + 1]) * idia[i];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 2 * nseg; idx += blockDim.x) {
+    const int j = idx >> 1, s = idx & 1;
+    const double* y = y_all + s * N;
+    const double M0 = M[s][j], M1 = M[s][j + 1];
+    double* c = coef + j * 8 + s * 4;
+    c[0] = y[j];
+    c[1] = (y[j + 1] - y[j]) * ih[j] - h[j] * (2.0 * M0 + M1) / 6.0;
+    c[2] = 0.5 * M0;
+    c[3] = (M1 - M0) * ih[j] / 6.0;
+  }
+  for (int k = threadIdx.x; k < 2 * n_res; k += blockDim.x) coef[8 * nseg + k] = params[k];
+}
+
+void launch_prepare(const Model& m, const double* params, const double* lu, double* coef,
+                    cudaStream_t st) {
+  prepare_kernel<<<1, 64, 0, st>>>(m.n_res, m.kn.n, params, lu, coef);
+}
+
+}  // namespace mipwa

@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated for the method's accuracy targets):
+  * FP64 form: NLL within 1e-12 relative, gradient within 1e-8 (norm-wise
+    relative), per-event |A|^2 within 1e-12 relative;
+  * FP32-mixed form: per-event |A|^2 within 1e-5 relative of the oracle fed the
+    same float32-rounded (s12, s13); NLL within 1e-2 absolute at 10^7 events
+    (tested here at 10^6 events with the same bound);
+  * Dalitz-boundary classification: identical (an integer decision, both sides FP64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from tests import _problems as P
+
+pytestmark = pytest.mark.gpu
+
+lib_mod = pytest.importorskip("paper_1703_03284_gb300")
+from paper_1703_03284_gb300 import F32, F64, Likelihood, MipwaError  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1703_03284_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def make(name, data, norm, mode=F64):
+    lik = Likelihood(0, mode)
+    lik.set_spec(P.spec_by_name(name))
+    lik.set_events(torch.from_numpy(np.ascontiguousarray(data)).to(DEV))
+    lik.set_norm_sample(torch.from_numpy(np.ascontiguousarray(norm)).to(DEV))
+    return lik
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def grad_rel(g, gref):
+    return np.linalg.norm(g - gref) / np.linalg.norm(gref)
+
+
+# ------------------------------------------------------------------ FP64 form
+@pytest.mark.parametrize("which", ["true", "perturbed"])
+def test_fp64_small_config(which):
+    """10^4 accept-reject events, 10 knots, normalisation on the in-boundary
+    centres of a 100 x 100 grid; FP64 throughout."""
+    name = "pipipi_n10"
+    data, norm = P.data_sample(name, 10_000), P.grid_sample(name, 100)
+    spec = P.spec_by_name(name)
+    p = synth.true_params(spec) if which == "true" else synth.perturbed_params(spec, 3)
+    lik = make(name, data, norm)
+    v, g = lik.nll_grad(p)
+    vr, gr = P.oracle_for(name).nll_grad(p, data, norm)
+    assert rel(v, vr) < 1e-12
+    assert grad_rel(g, gr) < 1e-8
+    assert lik.nll(p) == v
+
+
+@pytest.mark.parametrize("name", ["pipipi_n30", "pipipi_n40", "kpipi_n40"])
+def test_fp64_models(name):
+    data, norm = P.data_sample(name, 20_000), P.uniform_sample(name, 30_000)
+    spec = P.spec_by_name(name)
+    p = synth.perturbed_params(spec, 5)
+    lik = make(name, data, norm)
+    v, g = lik.nll_grad(p)
+    vr, gr = P.oracle_for(name).nll_grad(p, data, norm)
+    assert rel(v, vr) < 1e-12
+    assert grad_rel(g, gr) < 1e-8
+
+
+@pytest.mark.parametrize("nd,nn", [(1, 1), (255, 257), (257, 4097), (1023, 1), (5000, 300)])
+def test_fp64_ragged_sizes(nd, nn):
+    name = "pipipi_n10"
+    data = P.data_sample(name, 6000)[:nd]
+    norm = P.uniform_sample(name, 5000)[:nn]
+    p = synth.perturbed_params(P.spec_by_name(name), 7)
+    lik = make(name, data, norm)
+    v, g = lik.nll_grad(p)
+    vr, gr = P.oracle_for(name).nll_grad(p, data, norm)
+    assert rel(v, vr) < 1e-12
+    assert grad_rel(g, gr) < 1e-8
+
+
+def test_empty_data_sample():
+    name = "pipipi_n10"
+    norm = P.grid_sample(name, 50)
+    p = synth.true_params(P.spec_by_name(name))
+    lik = make(name, np.zeros((0, 2)), norm)
+    v, g = lik.nll_grad(p)
+    assert v == 0.0
+    assert np.all(g == 0.0)
+
+
+def test_fp64_amp2_per_event():
+    for name in ("pipipi_n10", "kpipi_n40"):
+        spec = P.spec_by_name(name)
+        o = P.oracle_for(name)
+        ev = P.uniform_sample(name, 50_001)
+        p = synth.perturbed_params(spec, 9)
+        lik = Likelihood(0, F64)
+        lik.set_spec(spec)
+        got = lik.amp2(p, torch.from_numpy(ev).to(DEV)).cpu().numpy()
+        want = o.amp2(p, ev)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+        # outside points have no support
+        box = spec.s_lo + (spec.s_hi - spec.s_lo) * np.random.default_rng(4).random((4000, 2))
+        out = lik.amp2(p, torch.from_numpy(box).to(DEV)).cpu().numpy()
+        np.testing.assert_allclose(out, o.density(p, box), rtol=1e-12, atol=0)
+
+
+def test_inside_matches_oracle():
+    for name in ("pipipi_n10", "kpipi_n40"):
+        spec = P.spec_by_name(name)
+        o = P.oracle_for(name)
+        rng = np.random.default_rng(21)
+        box = spec.s_lo - 0.05 + (spec.s_hi - spec.s_lo + 0.1) * rng.random((200_000, 2))
+        lik = Likelihood(0, F64)
+        lik.set_masses(spec.mD, spec.m1, spec.m2)
+        got = lik.inside(torch.from_numpy(box).to(DEV)).cpu().numpy()
+        np.testing.assert_array_equal(got, o.inside(box))
+        got32 = lik.inside(torch.from_numpy(box.astype(np.float32)).to(DEV)).cpu().numpy()
+        np.testing.assert_array_equal(got32, o.inside(box.astype(np.float32).astype(np.float64)))
+
+
+def test_set_events_rejects_outside_and_keeps_state():
+    name = "pipipi_n10"
+    data, norm = P.data_sample(name, 3000), P.grid_sample(name, 50)
+    p = synth.true_params(P.spec_by_name(name))
+    lik = make(name, data, norm)
+    v0 = lik.nll(p)
+    bad = data.copy()
+    bad[[5, 17, 2000]] = [[0.01, 0.01], [3.5, 0.5], [2.9, 2.9]]
+    with pytest.raises(MipwaError) as e:
+        lik.set_events(torch.from_numpy(bad).to(DEV))
+    assert e.value.status == -2 and e.value.n_outside == 3
+    assert lik.nll(p) == v0
+
+
+def test_call_order_and_argument_errors():
+    name = "pipipi_n10"
+    spec = P.spec_by_name(name)
+    lik = Likelihood(0, F64)
+    with pytest.raises(MipwaError) as e:
+        lik.set_events(np.zeros((3, 2)))
+    assert e.value.status == -6
+    lik.set_masses(spec.mD, spec.m1, spec.m2)
+    with pytest.raises(MipwaError) as e:
+        lik.set_model(spec.resonances, spec.knots[::-1], spec.r_res, spec.r_D)
+    assert e.value.status == -1
+    with pytest.raises(MipwaError) as e:
+        lik.set_model(((0.1, 0.1, 1),), spec.knots, spec.r_res, spec.r_D)  # below threshold
+    assert e.value.status == -1
+    lik.set_model(spec.resonances, spec.knots, spec.r_res, spec.r_D)
+    with pytest.raises(MipwaError) as e:
+        lik.nll(synth.true_params(spec))
+    assert e.value.status == -6
+    lik.set_events(P.data_sample(name, 100))
+    with pytest.raises(MipwaError) as e:
+        lik.set_norm_sample(np.zeros((0, 2)))
+    assert e.value.status == -1
+    lik.set_norm_sample(P.grid_sample(name, 30))
+    p = synth.true_params(spec)
+    p[3] = np.nan
+    with pytest.raises(MipwaError) as e:
+        lik.nll(p)
+    assert e.value.status == -1
+
+
+def test_nonpositive_amplitude_is_an_error():
+    name = "pipipi_n10"
+    lik = make(name, P.data_sample(name, 500), P.grid_sample(name, 40))
+    with pytest.raises(MipwaError) as e:
+        lik.nll(np.zeros(P.spec_by_name(name).n_params))
+    assert e.value.status == -3
+
+
+def test_nonuniform_knots_and_spin0():
+    spec = synth.ModelSpec(name="custom", mD=synth.M_D, m1=synth.M_PI, m2=synth.M_PI,
+                           resonances=((0.77526, 0.1491, 1), (0.98, 0.06, 0), (1.2755, 0.1867, 2)),
+                           knots=(0.078, 0.2, 0.45, 0.8, 0.95, 1.3, 1.9, 2.5, 2.987))
+    import oracle
+    o = oracle.Oracle(spec)
+    ins = synth.numpy_density(lambda x: o.inside(x).astype(np.float64))
+    pts = synth.uniform_in_plot(spec, 20_000, ins, seed=5).numpy()
+    data, norm = pts[:8000], pts[8000:]
+    rng = np.random.default_rng(2)
+    p = np.concatenate([[0.2, 0.0, 0.1, 0.3, 0.3, -0.1], 1 + 0.3 * rng.random(9),
+                        np.linspace(0, 2.5, 9)])
+    lik = Likelihood(0, F64)
+    lik.set_spec(spec)
+    lik.set_events(data)
+    lik.set_norm_sample(norm)
+    v, g = lik.nll_grad(p)
+    vr, gr = o.nll_grad(p, data, norm)
+    assert rel(v, vr) < 1e-12
+    assert grad_rel(g, gr) < 1e-8
+
+
+def test_fp64_gradient_central_differences():
+    name = "kpipi_n40"
+    lik = make(name, P.data_sample(name, 10_000), P.uniform_sample(name, 10_000))
+    p = synth.perturbed_params(P.spec_by_name(name), 13)
+    _, g = lik.nll_grad(p)
+    h = 1e-6
+    fd = np.empty_like(p)
+    for k in range(len(p)):
+        e = np.zeros_like(p)
+        e[k] = h
+        fd[k] = (lik.nll(p + e) - lik.nll(p - e)) / (2 * h)
+    assert grad_rel(g, fd) < 1e-6
+
+
+def test_nll_is_deterministic():
+    name = "pipipi_n40"
+    lik = make(name, P.data_sample(name, 100_000), P.uniform_sample(name, 100_000))
+    p = synth.perturbed_params(P.spec_by_name(name), 1)
+    a = [lik.nll(p) for _ in range(3)]
+    assert a[0] == a[1] == a[2]
+    g = [lik.nll_grad(p)[1] for _ in range(2)]
+    np.testing.assert_allclose(g[0], g[1], rtol=1e-13, atol=1e-13 * np.abs(g[0]).max())
+
+
+def test_autograd_function_matches_gradient():
+    from paper_1703_03284_gb300.autograd import MipwaNLL
+
+    name = "pipipi_n10"
+    lik = make(name, P.data_sample(name, 4000), P.grid_sample(name, 60))
+    p0 = synth.perturbed_params(P.spec_by_name(name), 2)
+    p = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    y = MipwaNLL.apply(p, lik)
+    (3.0 * y).backward()
+    v, g = lik.nll_grad(p0)
+    assert float(y) == v
+    np.testing.assert_allclose(p.grad.numpy(), 3.0 * g, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- FP32 form
+def test_fp32_amp2_per_event():
+    for name in ("pipipi_n40", "kpipi_n40"):
+        spec = P.spec_by_name(name)
+        o = P.oracle_for(name)
+        ev32 = P.uniform_sample(name, 200_000, f32=True)
+        p = synth.perturbed_params(spec, 9)
+        lik = Likelihood(0, F32)
+        lik.set_spec(spec)
+        got = lik.amp2(p, torch.from_numpy(ev32).to(DEV)).cpu().numpy()
+        want = o.amp2(p, ev32.astype(np.float64))
+        err = np.abs(got / want - 1)
+        assert err.max() < 1e-5, err.max()
+
+
+def test_fp32_nll_1e6():
+    name = "pipipi_n40"
+    data = P.data_sample(name, 1_000_000, f32=True)
+    norm = P.uniform_sample(name, 1_000_000, f32=True)
+    spec = P.spec_by_name(name)
+    for p in (synth.true_params(spec), synth.perturbed_params(spec, 4)):
+        lik = make(name, data, norm, mode=F32)
+        v, g = lik.nll_grad(p)
+        vr, gr = P.oracle_for(name).nll_grad(p, data.astype(np.float64), norm.astype(np.float64))
+        assert abs(v - vr) < 1e-2, (v, vr)
+        assert grad_rel(g, gr) < 1e-4
