@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -27,12 +28,15 @@ struct mipwa_ctx {
   double* d_lu = nullptr;
   double* d_params = nullptr;
   double* d_coef = nullptr;
+  float* d_coef32 = nullptr;
   double* d_out = nullptr;
   int* d_flags = nullptr;
   unsigned int* d_counter = nullptr;
   unsigned long long* d_count = nullptr;
   double* d_partials = nullptr;
   size_t partials_cap = 0;  // doubles
+  int* d_sortwork = nullptr;
+  size_t sortwork_cap = 0;  // bytes
   double* h_stage = nullptr;  // pinned: params in, results out
   // samples (double-buffered so that a rejected set_* keeps the old one)
   struct Sample {
@@ -43,6 +47,7 @@ struct mipwa_ctx {
     int64_t n = 0;
     int dtype = MIPWA_F64;
     bool set = false;
+    bool sorted = false;  // grouped by spline cell of the current knots
   } data, norm;
   int64_t launches = 0;
   bool timing = false;
@@ -86,11 +91,13 @@ double kallen_sqrt(double x, double a, double b) {
   return std::sqrt(l);
 }
 
-// Fill the double and float constant blocks from masses, resonances and radii.
+// Fill the FP64 and FP32 constant blocks from masses, resonances and radii.
 void derive(Model& m, const mipwa_resonance* res, int n_res, double r_res, double r_D) {
   const double M = m.mD, m1 = m.m1, m2 = m.m2, m3 = m.m2;
-  Consts<double>& d = m.cd;
-  Consts<float>& f = m.cf;
+  ConstsD& d = m.cd;
+  ConstsF& f = m.cf;
+  d = ConstsD{};
+  f = ConstsF{};
   d.thr_p = (m1 + m2) * (m1 + m2);
   d.thr_m = (m1 - m2) * (m1 - m2);
   d.pthr_p = (M + m3) * (M + m3);
@@ -99,12 +106,8 @@ void derive(Model& m, const mipwa_resonance* res, int n_res, double r_res, doubl
   d.zc1 = (M * M - m3 * m3) * (m2 * m2 - m1 * m1);
   d.r2_res = r_res * r_res;
   d.r2_D = r_D * r_D;
-  d.thr_p_lo = d.thr_m_lo = d.pthr_p_lo = d.pthr_m_lo = d.sigma_lo = 0.0;
-  for (int r = 0; r < kMaxRes; ++r) {
-    d.m2[r] = d.m2_lo[r] = d.g[r] = d.nR[r] = d.nD[r] = 0.0;
-    d.L[r] = 0;
-  }
   m.n_res = n_res;
+  for (int r = 0; r < kMaxRes; ++r) m.cscale[r] = 1.0;
   for (int r = 0; r < n_res; ++r) {
     const double mr = res[r].mass, G = res[r].width;
     const int L = res[r].spin;
@@ -116,20 +119,19 @@ void derive(Model& m, const mipwa_resonance* res, int n_res, double r_res, doubl
     d.g[r] = mr * mr * G / std::pow(q0, 2 * L + 1);
     d.nR[r] = L == 1 ? 1.0 + z0R : (L == 2 ? z0R * z0R + 3.0 * z0R + 9.0 : 1.0);
     d.nD[r] = L == 1 ? 1.0 + z0D : (L == 2 ? z0D * z0D + 3.0 * z0D + 9.0 : 1.0);
+    m.cscale[r] = std::sqrt(d.nR[r] * d.nD[r]) / (L == 2 ? 3.0 : 1.0);
   }
   split(d.thr_p, f.thr_p, f.thr_p_lo);
   split(d.thr_m, f.thr_m, f.thr_m_lo);
   split(d.pthr_p, f.pthr_p, f.pthr_p_lo);
   split(d.pthr_m, f.pthr_m, f.pthr_m_lo);
   split(d.sigma, f.sigma, f.sigma_lo);
-  f.zc1 = (float)d.zc1;
-  f.r2_res = (float)d.r2_res;
-  f.r2_D = (float)d.r2_D;
+  split(d.zc1, f.zc1, f.zc1_lo);
+  split(d.r2_res, f.r2_res, f.r2_res_lo);
+  split(d.r2_D, f.r2_D, f.r2_D_lo);
   for (int r = 0; r < kMaxRes; ++r) {
     split(d.m2[r], f.m2[r], f.m2_lo[r]);
-    f.g[r] = (float)d.g[r];
-    f.nR[r] = (float)d.nR[r];
-    f.nD[r] = (float)d.nD[r];
+    split(d.g[r] * d.nR[r], f.K[r], f.K_lo[r]);
     f.L[r] = d.L[r];
   }
 }
@@ -198,6 +200,19 @@ int grid_for(mipwa_ctx* c, int64_t n) {
   return g < 1 ? 1 : (int)g;
 }
 
+// Reorder the events of `src` (n of them) into `dst` grouped by spline cell.
+int sort_into(mipwa_ctx* c, const void* src, int64_t n, int dtype, void* dst) {
+  size_t ints = 0;
+  sort_workspace_ints(c->model.kn.n, &ints);
+  int rc = ensure(c, (void**)&c->d_sortwork, &c->sortwork_cap, ints * sizeof(int));
+  if (rc) return rc;
+  CK(c, launch_sort(dtype == MIPWA_F32, c->model.kn, src, n, dst, c->d_sortwork, c->stream));
+  c->launches += 3;
+  return MIPWA_OK;
+}
+
+bool sortable(int64_t n) { return n > 1 && n < (int64_t)0x7fffffff; }
+
 int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n, int dtype,
                int on_device, int64_t* n_outside, bool allow_empty) {
   int rc = check_ctx(c);
@@ -232,11 +247,37 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
     return fail(c, MIPWA_EOUTSIDE, "%llu of %lld events lie outside the Dalitz plot", outside,
                 (long long)n);
   }
-  std::swap(smp.cur, smp.spare);
-  std::swap(smp.cur_cap, smp.spare_cap);
+  smp.sorted = false;
+  if (c->have_model && sortable(n)) {
+    // the old sample is no longer needed: sort the validated copy into it
+    rc = ensure(c, &smp.cur, &smp.cur_cap, bytes);
+    if (rc) return rc;
+    rc = sort_into(c, smp.spare, n, dtype, smp.cur);
+    if (rc) return rc;
+    CK(c, cudaStreamSynchronize(c->stream));
+    smp.sorted = true;
+  } else {
+    std::swap(smp.cur, smp.spare);
+    std::swap(smp.cur_cap, smp.spare_cap);
+  }
   smp.n = n;
   smp.dtype = dtype;
   smp.set = true;
+  return MIPWA_OK;
+}
+
+// Re-group a stored sample for the current knots (after set_model).
+int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
+  if (!smp.set || !sortable(smp.n)) return MIPWA_OK;
+  const size_t bytes = (size_t)smp.n * ev_bytes(smp.dtype);
+  int rc = ensure(c, &smp.spare, &smp.spare_cap, bytes);
+  if (rc) return rc;
+  rc = sort_into(c, smp.cur, smp.n, smp.dtype, smp.spare);
+  if (rc) return rc;
+  CK(c, cudaStreamSynchronize(c->stream));
+  std::swap(smp.cur, smp.spare);
+  std::swap(smp.cur_cap, smp.spare_cap);
+  smp.sorted = true;
   return MIPWA_OK;
 }
 
@@ -254,7 +295,9 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
     if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
   const int f32 = c->mode == MIPWA_F32;
   const int ev32 = c->norm.dtype == MIPWA_F32;
-  const int per_sm = eval_blocks_per_sm(f32, ev32, want_grad);
+  // one block count for both variants, so nll and nll_grad sum identically
+  const int per_sm = std::min(eval_blocks_per_sm(f32, ev32, false),
+                              eval_blocks_per_sm(f32, ev32, true));
   int total = c->sm_count * per_sm;
   const int64_t need_d = (c->data.n + kThreads - 1) / kThreads;
   const int64_t need_n = (c->norm.n + kThreads - 1) / kThreads;
@@ -278,7 +321,7 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, P * sizeof(double), cudaMemcpyHostToDevice,
                         c->stream));
   CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
-  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->stream);
+  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->d_coef32, c->stream);
   CK(c, cudaGetLastError());
   EvalArgs a;
   a.data = c->data.cur;
@@ -289,6 +332,7 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   a.nb_norm = nb_n;
   a.n_params = P;
   a.coef = c->d_coef;
+  a.coef32 = c->d_coef32;
   a.lu = c->d_lu;
   a.partials = c->d_partials;
   a.counter = c->d_counter;
@@ -350,6 +394,7 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
   if (cudaMalloc(&c->d_lu, SplineLU::size(kMaxKnots) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_params, P * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_coef, coef_size(kMaxKnots, kMaxRes) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_coef32, coef32_size(kMaxKnots, kMaxRes) * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&c->d_out, (1 + P) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_counter, sizeof(unsigned int)) != cudaSuccess ||
@@ -367,9 +412,10 @@ void mipwa_destroy(mipwa_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (void* p : {(void*)c->d_lu, (void*)c->d_params, (void*)c->d_coef, (void*)c->d_out,
+  for (void* p : {(void*)c->d_lu, (void*)c->d_params, (void*)c->d_coef, (void*)c->d_coef32,
+                  (void*)c->d_out,
                   (void*)c->d_flags, (void*)c->d_counter, (void*)c->d_count,
-                  (void*)c->d_partials, c->data.cur, c->data.spare, c->norm.cur,
+                  (void*)c->d_partials, (void*)c->d_sortwork, c->data.cur, c->data.spare, c->norm.cur,
                   c->norm.spare})
     if (p) cudaFree(p);
   if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -444,6 +490,8 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   kn.s0 = knots[0];
   kn.h = (knots[n_knots - 1] - knots[0]) / (n_knots - 1);
   kn.inv_h = 1.0 / kn.h;
+  kn.s0_f = (float)kn.s0;
+  kn.inv_h_f = (float)kn.inv_h;
   kn.uniform = 1;
   const double scale = std::fabs(knots[0]) + std::fabs(knots[n_knots - 1]);
   for (int k = 0; k < n_knots; ++k)
@@ -457,7 +505,9 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   c->model = m;
   c->n_params = 2 * n_res + 2 * n_knots;
   c->have_model = true;
-  return MIPWA_OK;
+  rc = resort(c, c->data);
+  if (rc) return rc;
+  return resort(c, c->norm);
 }
 
 int mipwa_set_events(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, int on_device,
@@ -497,10 +547,10 @@ int mipwa_amp2(mipwa_ctx* c, const double* params, const void* ev, int64_t n, in
   std::memcpy(c->h_stage, params, c->n_params * sizeof(double));
   CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, c->n_params * sizeof(double),
                         cudaMemcpyHostToDevice, c->stream));
-  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->stream);
+  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->d_coef32, c->stream);
   CK(c, cudaGetLastError());
-  CK(c, launch_amp2(c->mode == MIPWA_F32, dtype == MIPWA_F32, c->model, c->d_coef, ev, n, out,
-                    grid_for(c, n), c->stream));
+  CK(c, launch_amp2(c->mode == MIPWA_F32, dtype == MIPWA_F32, c->model, c->d_coef, c->d_coef32,
+                    ev, n, out, grid_for(c, n), c->stream));
   c->launches += 2;
   CK(c, cudaStreamSynchronize(c->stream));
   return MIPWA_OK;

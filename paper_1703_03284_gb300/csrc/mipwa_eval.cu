@@ -18,28 +18,6 @@
 
 namespace mipwa {
 
-template <typename T>
-__device__ __forceinline__ const Consts<T>& consts(const Model& m);
-template <>
-__device__ __forceinline__ const Consts<double>& consts<double>(const Model& m) {
-  return m.cd;
-}
-template <>
-__device__ __forceinline__ const Consts<float>& consts<float>(const Model& m) {
-  return m.cf;
-}
-
-template <typename EvT>
-struct Ev;
-template <>
-struct Ev<double2> {
-  using type = double2;
-};
-template <>
-struct Ev<float2> {
-  using type = float2;
-};
-
 // Per-thread running sums: plain FP64, or Kahan-compensated FP32.
 template <typename T>
 struct Acc;
@@ -53,21 +31,17 @@ template <>
 struct Acc<float> {
   float s = 0.0f, c = 0.0f;
   __device__ __forceinline__ void add(float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-template <typename T>
-struct EvalSmem {
-  T coef[kMaxSeg * 8];
-  T knot_hi[kMaxKnots];
-  T knot_lo[kMaxKnots];
-  T cre[kMaxRes];
-  T cim[kMaxRes];
+// Shared memory of the event kernels: the model's per-evaluation data (form
+// dependent) plus the reduction scratch.
+struct SmemCommon {
   float binf[kMaxSeg * 8];    // FP32 form: bins of the current flush window
   double bind[kMaxSeg * 8];   // FP64 bins of the polynomial adjoints
   double red[kThreads / 32][1 + 2 * kMaxRes];
@@ -78,63 +52,150 @@ struct EvalSmem {
   int is_last;
 };
 
-// Stage coefficients, knots and c_r in shared memory.
 template <typename T>
-__device__ void stage(EvalSmem<T>& sm, const Model& m, const double* coef) {
+struct EvalSmem;
+template <>
+struct EvalSmem<double> : SmemCommon {
+  double coef[kMaxSeg * 8];  // magnitude and phase cubics, about s_j
+  double knot[kMaxKnots];
+  double cre[kMaxRes], cim[kMaxRes];
+};
+template <>
+struct EvalSmem<float> : SmemCommon {
+  __align__(16) float coef[kMaxSeg * 16];  // hi/lo cubics about float(s_j)
+  float knot[kMaxKnots];     // float(s_j)
+  float knot_lo[kMaxKnots];  // s_j - float(s_j)
+  float cre[kMaxRes], cre_lo[kMaxRes], cim[kMaxRes], cim_lo[kMaxRes];
+};
+
+struct EvalCoefs {
+  const double* coef;   // FP64 form
+  const float* coef32;  // FP32 form
+};
+
+__device__ void stage(EvalSmem<double>& sm, const Model& m, const EvalCoefs& cf) {
   const int nseg = m.kn.n - 1;
-  for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) sm.coef[i] = (T)coef[i];
-  for (int i = threadIdx.x; i < m.kn.n; i += blockDim.x) {
-    const double s = m.kn.s[i];
-    const T hi = (T)s;
-    sm.knot_hi[i] = hi;
-    sm.knot_lo[i] = (T)(s - (double)hi);
-  }
+  for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) sm.coef[i] = cf.coef[i];
+  for (int i = threadIdx.x; i < m.kn.n; i += blockDim.x) sm.knot[i] = m.kn.s[i];
   if (threadIdx.x < m.n_res) {
-    sm.cre[threadIdx.x] = (T)coef[nseg * 8 + 2 * threadIdx.x];
-    sm.cim[threadIdx.x] = (T)coef[nseg * 8 + 2 * threadIdx.x + 1];
+    sm.cre[threadIdx.x] = cf.coef[nseg * 8 + 2 * threadIdx.x];
+    sm.cim[threadIdx.x] = cf.coef[nseg * 8 + 2 * threadIdx.x + 1];
   }
 }
 
-// Forward amplitude of one event. Returns A; fills the Bose-symmetrised
-// Breit-Wigner basis B[r] and the S-wave pieces of both channels.
+__device__ void stage(EvalSmem<float>& sm, const Model& m, const EvalCoefs& cf) {
+  const int nseg = m.kn.n - 1;
+  for (int i = threadIdx.x; i < nseg * 16; i += blockDim.x) sm.coef[i] = cf.coef32[i];
+  for (int i = threadIdx.x; i < m.kn.n; i += blockDim.x) {
+    const float hi = (float)m.kn.s[i];
+    sm.knot[i] = hi;
+    sm.knot_lo[i] = (float)(m.kn.s[i] - (double)hi);
+  }
+  if (threadIdx.x < m.n_res) {
+    const float* c = cf.coef32 + nseg * 16 + 4 * threadIdx.x;
+    sm.cre[threadIdx.x] = c[0];
+    sm.cre_lo[threadIdx.x] = c[1];
+    sm.cim[threadIdx.x] = c[2];
+    sm.cim_lo[threadIdx.x] = c[3];
+  }
+}
+
+// S-wave pieces of one channel kept for the adjoint.
 template <typename T>
 struct SwavePart {
   int j;
   T t, a, cs, sn;
 };
 
-template <typename T>
-__device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& sm, T s12,
-                                             T s13, Cplx<T>* B, SwavePart<T>& w12,
-                                             SwavePart<T>& w13) {
-  const Consts<T>& c = consts<T>(m);
-  const Chan<T> k12 = channel(c, s12);
-  const Chan<T> k13 = channel(c, s13);
-  T z1a, z2a, z1b, z2b;
-  zemach(c, k12, s13, z1a, z2a);
-  zemach(c, k13, s12, z1b, z2b);
-  Cplx<T> A{T(0), T(0)};
+// Forward amplitude of one event, FP64 form. Fills the Bose-symmetrised
+// Breit-Wigner basis B[r] and the S-wave pieces of both channels.
+__device__ __forceinline__ Cplx<double> amplitude(const Model& m, const EvalSmem<double>& sm,
+                                                  double s12, double s13, Cplx<double>* B,
+                                                  SwavePart<double>& w12,
+                                                  SwavePart<double>& w13) {
+  const ConstsD& c = m.cd;
+  const ChanD k12 = channel_d(c, s12);
+  const ChanD k13 = channel_d(c, s13);
+  double z1a, z2a, z1b, z2b;
+  zemach_d(c, k12, s13, z1a, z2a);
+  zemach_d(c, k13, s12, z1b, z2b);
+  Cplx<double> A{0.0, 0.0};
 #pragma unroll
   for (int r = 0; r < kMaxRes; ++r) {
     if (r < m.n_res) {
-      const Cplx<T> u = bw_term(c, r, k12, z1a, z2a);
-      const Cplx<T> v = bw_term(c, r, k13, z1b, z2b);
+      const Cplx<double> u = bw_d(c, r, k12, z1a, z2a);
+      const Cplx<double> v = bw_d(c, r, k13, z1b, z2b);
       B[r].re = u.re + v.re;
       B[r].im = u.im + v.im;
       A.re += sm.cre[r] * B[r].re - sm.cim[r] * B[r].im;
       A.im += sm.cre[r] * B[r].im + sm.cim[r] * B[r].re;
     }
   }
-  w12.j = segment(m.kn, sm.knot_hi, sm.knot_lo, s12, w12.t);
-  w13.j = segment(m.kn, sm.knot_hi, sm.knot_lo, s13, w13.t);
-  w12.a = horner(&sm.coef[w12.j * 8], w12.t);
-  w13.a = horner(&sm.coef[w13.j * 8], w13.t);
-  const T ph12 = horner(&sm.coef[w12.j * 8 + 4], w12.t);
-  const T ph13 = horner(&sm.coef[w13.j * 8 + 4], w13.t);
-  dsincos(ph12, &w12.sn, &w12.cs);
-  dsincos(ph13, &w13.sn, &w13.cs);
-  A.re += w12.a * w12.cs + w13.a * w13.cs;
-  A.im += w12.a * w12.sn + w13.a * w13.sn;
+  SwavePart<double>* ws[2] = {&w12, &w13};
+  const double ss[2] = {s12, s13};
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch) {
+    SwavePart<double>& w = *ws[ch];
+    w.j = segment_of(m.kn, sm.knot, ss[ch]);
+    w.t = ss[ch] - sm.knot[w.j];
+    const double* a = &sm.coef[w.j * 8];
+    w.a = ((a[3] * w.t + a[2]) * w.t + a[1]) * w.t + a[0];
+    const double ph = ((a[7] * w.t + a[6]) * w.t + a[5]) * w.t + a[4];
+    sincos(ph, &w.sn, &w.cs);
+    A.re += w.a * w.cs;
+    A.im += w.a * w.sn;
+  }
+  return A;
+}
+
+// FP32 form: cubic value as an exact pair hi + lo: the hi-coefficient Horner
+// tail t (a1 + a2 t + a3 t^2) plus a0 by TwoSum, the lo-coefficient Horner
+// added to the low part.
+__device__ __forceinline__ F2 cubic_hl(const float4 hi, const float4 lo, float t) {
+  const float tq = fmaf(fmaf(hi.w, t, hi.z), t, hi.y) * t;
+  const float pl = fmaf(fmaf(fmaf(lo.w, t, lo.z), t, lo.y), t, lo.x);
+  F2 v = two_sum(hi.x, tq);
+  v.lo += pl;
+  return v;
+}
+
+__device__ __forceinline__ Cplx<float> amplitude(const Model& m, const EvalSmem<float>& sm,
+                                                 float s12, float s13, Cplx<float>* B,
+                                                 SwavePart<float>& w12, SwavePart<float>& w13) {
+  const ConstsF& c = m.cf;
+  const ChanF k12 = channel_f(c, s12);
+  const ChanF k13 = channel_f(c, s13);
+  F2 z1a, z1b;
+  float z2a, z2b;
+  zemach_f(c, k12, s13, z1a, z2a);
+  zemach_f(c, k13, s12, z1b, z2b);
+  Cplx<float> A{0.0f, 0.0f};
+#pragma unroll
+  for (int r = 0; r < kMaxRes; ++r) {
+    if (r < m.n_res) {
+      const Cplx<float> u = bw_f(c, r, k12, z1a, z2a);
+      const Cplx<float> v = bw_f(c, r, k13, z1b, z2b);
+      B[r].re = u.re + v.re;
+      B[r].im = u.im + v.im;
+      A.re += mul_hl(sm.cre[r], sm.cre_lo[r], B[r].re) - mul_hl(sm.cim[r], sm.cim_lo[r], B[r].im);
+      A.im += mul_hl(sm.cre[r], sm.cre_lo[r], B[r].im) + mul_hl(sm.cim[r], sm.cim_lo[r], B[r].re);
+    }
+  }
+  SwavePart<float>* ws[2] = {&w12, &w13};
+  const float ss[2] = {s12, s13};
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch) {
+    SwavePart<float>& w = *ws[ch];
+    w.j = segment_of(m.kn, sm.knot, ss[ch]);
+    w.t = __fsub_rn(ss[ch], sm.knot[w.j]);  // exact (Sterbenz) on the knot grids used here
+    const float4* c4 = reinterpret_cast<const float4*>(&sm.coef[w.j * 16]);
+    const F2 a = cubic_hl(c4[0], c4[1], w.t);
+    const F2 ph = cubic_hl(c4[2], c4[3], w.t);
+    sincos_cw(ph.hi, ph.lo, &w.sn, &w.cs);
+    w.a = a.hi;
+    A.re += mul_hl(a.hi, a.lo, w.cs);
+    A.im += mul_hl(a.hi, a.lo, w.sn);
+  }
   return A;
 }
 
@@ -147,23 +208,75 @@ __device__ __forceinline__ void bin_add(EvalSmem<T>& sm, int idx, T v) {
   }
 }
 
-// Scatter the adjoint of one channel's S-wave into the polynomial bins:
-// d|A|^2/d a(s) = 2 Re(A* e^{i phi}),  d|A|^2/d phi(s) = 2 a Re(A* i e^{i phi}).
+// Adjoint of one channel's S-wave, as the 8 contributions to its segment's
+// polynomial bins: d|A|^2/d a(s) = 2 Re(A* e^{i phi}) and
+// d|A|^2/d phi(s) = 2 a Re(A* i e^{i phi}), times t^m, t = s - s_j (the exact
+// knot: the FP32 form evaluates about float(s_j) and shifts back here).
 template <typename T>
-__device__ __forceinline__ void scatter_swave(EvalSmem<T>& sm, const SwavePart<T>& w,
-                                              Cplx<T> A, T wt) {
+__device__ __forceinline__ void swave_adjoint(const EvalSmem<T>& sm, const SwavePart<T>& w,
+                                              Cplx<T> A, T wt, T* v) {
   const T abar = T(2) * wt * (A.re * w.cs + A.im * w.sn);
   const T pbar = T(2) * wt * w.a * (A.im * w.cs - A.re * w.sn);
-  const T t1 = w.t, t2 = w.t * w.t, t3 = t2 * w.t;
-  const int base = w.j * 8;
-  bin_add(sm, base + 0, abar);
-  bin_add(sm, base + 1, abar * t1);
-  bin_add(sm, base + 2, abar * t2);
-  bin_add(sm, base + 3, abar * t3);
-  bin_add(sm, base + 4, pbar);
-  bin_add(sm, base + 5, pbar * t1);
-  bin_add(sm, base + 6, pbar * t2);
-  bin_add(sm, base + 7, pbar * t3);
+  T t1 = w.t;
+  if constexpr (std::is_same<T, float>::value) t1 = w.t - sm.knot_lo[w.j];
+  const T t2 = t1 * t1, t3 = t2 * t1;
+  v[0] = abar;
+  v[1] = abar * t1;
+  v[2] = abar * t2;
+  v[3] = abar * t3;
+  v[4] = pbar;
+  v[5] = pbar * t1;
+  v[6] = pbar * t2;
+  v[7] = pbar * t3;
+}
+
+// Sum 16 values over the warp so that lanes 2i and 2i+1 both end with the
+// total of value i (recursive halving: 8 + 4 + 2 + 1 + 1 shuffles).
+template <typename T>
+__device__ __forceinline__ T reduce_scatter16(const T (&v)[16], int lane) {
+  constexpr unsigned full = 0xffffffffu;
+  T a8[8], a4[4], a2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    a8[k] = (h16 ? v[k + 8] : v[k]) + __shfl_xor_sync(full, h16 ? v[k] : v[k + 8], 16);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    a4[k] = (h8 ? a8[k + 4] : a8[k]) + __shfl_xor_sync(full, h8 ? a8[k] : a8[k + 4], 8);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    a2[k] = (h4 ? a4[k + 2] : a4[k]) + __shfl_xor_sync(full, h4 ? a4[k] : a4[k + 2], 4);
+  T a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(full, h2 ? a2[0] : a2[1], 2);
+  a1 += __shfl_xor_sync(full, a1, 1);
+  return a1;
+}
+
+// Bin the S-wave adjoint of the warp's events. Events come sorted by spline
+// cell, so the warp's live events nearly always share (j12, j13): then the
+// 16 contributions are summed over the warp first and 16 lanes add one total
+// each. Otherwise every lane adds its own 16 values.
+template <typename T>
+__device__ __forceinline__ void bin_swave_warp(EvalSmem<T>& sm, bool valid, int j12, int j13,
+                                               const T (&v)[16]) {
+  constexpr unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int key = valid ? (j12 << 6) | j13 : -1;
+  const unsigned have = __ballot_sync(full, valid);
+  if (!have) return;
+  const int k0 = __shfl_sync(full, key, __ffs(have) - 1);
+  if (__all_sync(full, !valid || key == k0)) {
+    const T tot = reduce_scatter16(v, lane);
+    if ((lane & 1) == 0) {
+      const int idx = lane >> 1;
+      const int j = idx < 8 ? (k0 >> 6) : (k0 & 63);
+      bin_add(sm, j * 8 + (idx & 7), tot);
+    }
+  } else if (valid) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) bin_add(sm, j12 * 8 + k, v[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) bin_add(sm, j13 * 8 + k, v[8 + k]);
+  }
 }
 
 // The last block: reduce block rows in order, then -2 ln L, its gradient, and
@@ -193,7 +306,11 @@ __device__ void finalize(EvalSmem<T>& sm, const EvalArgs& a) {
     for (int col = 1 + threadIdx.x; col < W; col += blockDim.x)
       sm.fin_d[col] = -2.0 * sm.fin_d[col] + kappa * sm.fin_n[col];
     __syncthreads();
-    for (int k = threadIdx.x; k < 2 * R; k += blockDim.x) a.out[1 + k] = sm.fin_d[1 + k];
+    for (int k = threadIdx.x; k < 2 * R; k += blockDim.x) {
+      // FP32 form: the kernel accumulated against A_r / cscale_r
+      const double sc = std::is_same<T, float>::value ? m.cscale[k >> 1] : 1.0;
+      a.out[1 + k] = sm.fin_d[1 + k] * sc;
+    }
     // one thread per spline, in different warps
     const int sp = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 ? 1 : -1);
     if (sp >= 0) {
@@ -240,7 +357,7 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
   __shared__ EvalSmem<T> sm;
   const Model& m = a.model;
   const int R = m.n_res, nseg = m.kn.n - 1;
-  stage(sm, m, a.coef);
+  stage(sm, m, EvalCoefs{a.coef, a.coef32});
   if constexpr (GRAD) {
     for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) {
       sm.bind[i] = 0.0;
@@ -257,24 +374,34 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
   const int64_t stride = (int64_t)nb * kThreads;
 
   Acc<T> sum;
-  Acc<T> gc[2 * kMaxRes];
+  T gc[2 * kMaxRes];  // c_r adjoint: plain sums (gradient tolerance), FP64 per block
+#pragma unroll
+  for (int k = 0; k < 2 * kMaxRes; ++k) gc[k] = T(0);
+  long long sum_e = 0;  // FP32 form, data: sum of binary exponents of |A|^2
   int bad = 0;
   int iter = 0;
   for (int64_t base = (int64_t)b * kThreads; base < n; base += stride) {
     const int64_t i = base + threadIdx.x;
+    bool ok = false;
+    SwavePart<T> w12, w13;
+    Cplx<T> A{T(0), T(0)};
+    Cplx<T> B[kMaxRes];
+    T wt = T(1);
     if (i < n) {
       const EvT e = ev[i];
       const T s12 = (T)e.x, s13 = (T)e.y;
-      Cplx<T> B[kMaxRes];
-      SwavePart<T> w12, w13;
-      const Cplx<T> A = amplitude(m, sm, s12, s13, B, w12, w13);
+      A = amplitude(m, sm, s12, s13, B, w12, w13);
       const T A2 = A.re * A.re + A.im * A.im;
-      T wt = T(1);
-      bool ok;
       if (is_data) {
         ok = A2 > T(0) && isfinite(A2);
         if (ok) {
-          if constexpr (std::is_same<T, float>::value) sum.add(logf(A2)); else sum.add(log(A2));
+          if constexpr (std::is_same<T, float>::value) {
+            int ex;
+            sum.add(log_split(A2, ex));
+            sum_e += ex;
+          } else {
+            sum.add(log(A2));
+          }
           wt = T(1) / A2;
         }
       } else {
@@ -282,19 +409,24 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
         if (ok) sum.add(A2);
       }
       bad |= ok ? 0 : 1;
-      if constexpr (GRAD) {
-        if (ok) {
+    }
+    if constexpr (GRAD) {
+      T v[16];
+      if (ok) {
 #pragma unroll
-          for (int r = 0; r < kMaxRes; ++r) {
-            if (r < R) {
-              gc[2 * r].add(T(2) * wt * (A.re * B[r].re + A.im * B[r].im));
-              gc[2 * r + 1].add(T(2) * wt * (A.im * B[r].re - A.re * B[r].im));
-            }
+        for (int r = 0; r < kMaxRes; ++r) {
+          if (r < R) {
+            gc[2 * r] += T(2) * wt * (A.re * B[r].re + A.im * B[r].im);
+            gc[2 * r + 1] += T(2) * wt * (A.im * B[r].re - A.re * B[r].im);
           }
-          scatter_swave(sm, w12, A, wt);
-          scatter_swave(sm, w13, A, wt);
         }
+        swave_adjoint(sm, w12, A, wt, v);
+        swave_adjoint(sm, w13, A, wt, v + 8);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = T(0);
       }
+      bin_swave_warp(sm, ok, ok ? w12.j : 0, ok ? w13.j : 0, v);
     }
     if constexpr (GRAD && std::is_same<T, float>::value) {
       if (++iter == kFlushIters) {
@@ -320,7 +452,7 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
 #pragma unroll
   for (int k = 0; k < 1 + 2 * kMaxRes; ++k) {
     if (k < nred) {
-      double v = k == 0 ? sum.value() : gc[k - 1].value();
+      double v = k == 0 ? sum.value() + 0.69314718055994531 * (double)sum_e : (double)gc[k - 1];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
       if (lane == 0) sm.red[warp][k] = v;
@@ -352,10 +484,10 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
 // ----------------------------------------------------------- |A|^2 per event
 template <typename T, typename EvT>
 __global__ void __launch_bounds__(kThreads) amp2_kernel(const Model m, const double* coef,
-                                                        const EvT* ev, int64_t n,
-                                                        double* out) {
+                                                        const float* coef32, const EvT* ev,
+                                                        int64_t n, double* out) {
   __shared__ EvalSmem<T> sm;
-  stage(sm, m, coef);
+  stage(sm, m, EvalCoefs{coef, coef32});
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -425,18 +557,19 @@ int eval_blocks_per_sm(int compute_f32, int ev_f32, bool grad) {
 }
 
 cudaError_t launch_amp2(int compute_f32, int ev_f32, const Model& m, const double* coef,
-                        const void* ev, int64_t n, double* out, int grid, cudaStream_t st) {
+                        const float* coef32, const void* ev, int64_t n, double* out, int grid,
+                        cudaStream_t st) {
   if (compute_f32) {
     if (ev_f32)
-      amp2_kernel<float, float2><<<grid, kThreads, 0, st>>>(m, coef, (const float2*)ev, n, out);
+      amp2_kernel<float, float2><<<grid, kThreads, 0, st>>>(m, coef, coef32, (const float2*)ev, n, out);
     else
-      amp2_kernel<float, double2><<<grid, kThreads, 0, st>>>(m, coef, (const double2*)ev, n, out);
+      amp2_kernel<float, double2><<<grid, kThreads, 0, st>>>(m, coef, coef32, (const double2*)ev, n, out);
   } else {
     if (ev_f32)
-      amp2_kernel<double, float2><<<grid, kThreads, 0, st>>>(m, coef, (const float2*)ev, n, out);
+      amp2_kernel<double, float2><<<grid, kThreads, 0, st>>>(m, coef, coef32, (const float2*)ev, n, out);
     else
-      amp2_kernel<double, double2><<<grid, kThreads, 0, st>>>(m, coef, (const double2*)ev, n,
-                                                              out);
+      amp2_kernel<double, double2><<<grid, kThreads, 0, st>>>(m, coef, coef32,
+                                                              (const double2*)ev, n, out);
   }
   return cudaGetLastError();
 }

@@ -10,7 +10,7 @@
 namespace mipwa {
 
 constexpr int kThreads = 256;        // threads per block of the event kernels
-constexpr int kFlushIters = 8;       // FP32 form: grid-stride iterations between bin flushes
+constexpr int kFlushIters = 32;      // FP32 form: grid-stride iterations between bin flushes
 
 struct EvalArgs {
   const void* data;   // n_data pairs (s12, s13)
@@ -18,7 +18,8 @@ struct EvalArgs {
   int64_t n_data, n_norm;
   int nb_data, nb_norm;      // blocks given to each sample (gridDim.x = nb_data + nb_norm)
   int n_params;
-  const double* coef;        // prepare-kernel output (polynomial coefficients, c_r)
+  const double* coef;        // prepare-kernel output, FP64 form (cubics, c_r)
+  const float* coef32;       // prepare-kernel output, FP32 form (hi/lo cubics, c'_r)
   const double* lu;          // factored spline system (SplineLU layout)
   double* partials;          // gridDim.x rows of partial_width() doubles
   unsigned int* counter;     // finished-block ticket (zero between launches)
@@ -29,20 +30,21 @@ struct EvalArgs {
 
 enum { kFlagData = 1, kFlagNorm = 2, kFlagIntegral = 4 };
 
-// dtype codes match MIPWA_F64 / MIPWA_F32
-struct Launch {
-  int grid;
-  cudaStream_t stream;
-};
-
 void launch_prepare(const Model& m, const double* params, const double* lu, double* coef,
-                    cudaStream_t stream);
+                    float* coef32, cudaStream_t stream);
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t stream);
 cudaError_t launch_amp2(int compute_f32, int ev_f32, const Model& m, const double* coef,
-                        const void* ev, int64_t n, double* out, int grid, cudaStream_t stream);
+                        const float* coef32, const void* ev, int64_t n, double* out, int grid,
+                        cudaStream_t stream);
 cudaError_t launch_inside(int ev_f32, const Model& m, const void* ev, int64_t n, uint8_t* out,
                           unsigned long long* n_out, int grid, cudaStream_t stream);
 int eval_blocks_per_sm(int compute_f32, int ev_f32, bool grad);
+
+// Stable counting sort of n events from src into dst by spline cell (j12, j13);
+// work holds sort_workspace_ints() ints. n must be below 2^31.
+cudaError_t sort_workspace_ints(int n_knots, size_t* ints);
+cudaError_t launch_sort(int ev_f32, const Knots& kn, const void* src, int64_t n, void* dst,
+                        int* work, cudaStream_t stream);
 
 }  // namespace mipwa

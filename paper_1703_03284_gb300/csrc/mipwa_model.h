@@ -21,23 +21,37 @@ constexpr int kMaxRes = MIPWA_MAX_RES;
 constexpr int kMaxKnots = MIPWA_MAX_KNOTS;
 constexpr int kMaxSeg = kMaxKnots - 1;
 
-// Kinematic and resonance constants in arithmetic type T. For T = float the
-// *_lo members hold the rounding remainder of the double value (value = hi + lo),
-// so that differences such as s - (m1+m2)^2 or m_r^2 - s keep their accuracy
-// when s is close to the constant; for T = double they are unused.
-template <typename T>
-struct Consts {
-  T thr_p, thr_p_lo;    // (m1 + m2)^2
-  T thr_m, thr_m_lo;    // (m1 - m2)^2
-  T pthr_p, pthr_p_lo;  // (mD + m3)^2
-  T pthr_m, pthr_m_lo;  // (mD - m3)^2
-  T sigma, sigma_lo;    // mD^2 + m1^2 + m2^2 + m3^2
-  T zc1;                // (mD^2 - m3^2)(m2^2 - m1^2)
-  T r2_res, r2_D;       // Blatt-Weisskopf radii squared
-  T m2[kMaxRes], m2_lo[kMaxRes];  // m_r^2
-  T g[kMaxRes];         // m_r^2 Gamma_r / q0^(2L+1):  m_r Gamma(s) = g q^(2L+1)/sqrt(s) F_R^2
-  T nR[kMaxRes];        // numerator of F_R^2: 1 + z0 (L=1), z0^2 + 3 z0 + 9 (L=2)
-  T nD[kMaxRes];        // numerator of F_D^2, with z0 from p0 = p(m_r^2)
+// Kinematic and resonance constants of the plain FP64 form.
+struct ConstsD {
+  double thr_p;   // (m1 + m2)^2
+  double thr_m;   // (m1 - m2)^2
+  double pthr_p;  // (mD + m3)^2
+  double pthr_m;  // (mD - m3)^2
+  double sigma;   // mD^2 + m1^2 + m2^2 + m3^2
+  double zc1;     // (mD^2 - m3^2)(m2^2 - m1^2)
+  double r2_res, r2_D;   // Blatt-Weisskopf radii squared
+  double m2[kMaxRes];    // m_r^2
+  double g[kMaxRes];     // m_r^2 Gamma_r / q0^(2L+1):  m_r Gamma(s) = g q^(2L+1)/sqrt(s) F_R^2
+  double nR[kMaxRes];    // numerator of F_R^2: 1 + z0 (L=1), z0^2 + 3 z0 + 9 (L=2)
+  double nD[kMaxRes];    // numerator of F_D^2, with z0 from p0 = p(m_r^2)
+  int L[kMaxRes];
+};
+
+// Constants of the FP32-mixed form. Every constant that meets an input
+// (s12, s13 are float32 values) in a sum is held as an unevaluated pair
+// hi + lo of floats, and the differences s - C are formed exactly; otherwise
+// the rounding error of "grid value minus constant" is the same for every
+// event in a binade and biases -2 ln L by O(N eps). Multiplicative constants
+// that only scale a whole Breit-Wigner term (sqrt(nR nD), and 1/3 of the
+// D-wave Zemach factor) are folded into the coefficient c_r in FP64 instead.
+struct ConstsF {
+  float thr_p, thr_p_lo, thr_m, thr_m_lo;
+  float pthr_p, pthr_p_lo, pthr_m, pthr_m_lo;
+  float sigma, sigma_lo;
+  float zc1, zc1_lo;
+  float r2_res, r2_res_lo, r2_D, r2_D_lo;
+  float m2[kMaxRes], m2_lo[kMaxRes];
+  float K[kMaxRes], K_lo[kMaxRes];  // g nR:  m_r Gamma(s) = K q^(2L+1) / (sqrt(s) DR)
   int L[kMaxRes];
 };
 
@@ -46,14 +60,18 @@ struct Knots {
   int n;        // N
   int uniform;  // s_k = s0 + k h to rounding
   double s0, h, inv_h;
+  float s0_f, inv_h_f;  // the same, for segment lookup in FP32
   double s[kMaxKnots];
 };
 
 struct Model {
   int n_res;
   double mD, m1, m2;
-  Consts<double> cd;
-  Consts<float> cf;
+  ConstsD cd;
+  ConstsF cf;
+  // FP32 form: A_r is evaluated without the factor cscale_r = sqrt(nR nD)
+  // (divided by 3 for L = 2); the coefficient used is c_r * cscale_r.
+  double cscale[kMaxRes];
   Knots kn;
 };
 
@@ -70,6 +88,15 @@ struct SplineLU {
 // coef[j*8 + 4..7] = phase phi(s)   = sum_m beta_m t^m;
 // followed by 2R doubles (Re c_r, Im c_r).
 MIPWA_HD inline int coef_size(int n_knots, int n_res) { return 8 * (n_knots - 1) + 2 * n_res; }
+
+// FP32 form, written by the same kernel as floats: per segment 16 values,
+// magnitude hi[4] lo[4] then phase hi[4] lo[4], each cubic re-expanded about
+// the float-rounded knot float(s_j) so that t = s - float(s_j) is exact;
+// followed by 4 floats per resonance: (Re c'_r hi, lo, Im c'_r hi, lo),
+// c'_r = c_r cscale_r.
+MIPWA_HD inline int coef32_size(int n_knots, int n_res) {
+  return 16 * (n_knots - 1) + 4 * n_res;
+}
 
 // Width of one per-block partial-sum row:
 // [sum | Re/Im dA-weights of c_r (2R) | polynomial adjoints (8 (N-1))]

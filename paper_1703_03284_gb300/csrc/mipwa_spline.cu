@@ -15,8 +15,10 @@
 
 namespace mipwa {
 
-__global__ void prepare_kernel(const int n_res, const int N, const double* __restrict__ params,
-                               const double* __restrict__ lu, double* __restrict__ coef) {
+__global__ void prepare_kernel(const Model m, const double* __restrict__ params,
+                               const double* __restrict__ lu, double* __restrict__ coef,
+                               float* __restrict__ coef32) {
+  const int n_res = m.n_res, N = m.kn.n;
   __shared__ double M[2][kMaxKnots];
   const int nseg = N - 1, mm = N - 2;
   const double* h = lu;
@@ -45,18 +47,41 @@ __global__ void prepare_kernel(const int n_res, const int N, const double* __res
     const int j = idx >> 1, s = idx & 1;
     const double* y = y_all + s * N;
     const double M0 = M[s][j], M1 = M[s][j + 1];
+    double a[4];
+    a[0] = y[j];
+    a[1] = (y[j + 1] - y[j]) * ih[j] - h[j] * (2.0 * M0 + M1) / 6.0;
+    a[2] = 0.5 * M0;
+    a[3] = (M1 - M0) * ih[j] / 6.0;
     double* c = coef + j * 8 + s * 4;
-    c[0] = y[j];
-    c[1] = (y[j + 1] - y[j]) * ih[j] - h[j] * (2.0 * M0 + M1) / 6.0;
-    c[2] = 0.5 * M0;
-    c[3] = (M1 - M0) * ih[j] / 6.0;
+    for (int k = 0; k < 4; ++k) c[k] = a[k];
+    // FP32 form: the same cubic about float(s_j) (exact Taylor shift by d),
+    // each coefficient split into float hi + lo
+    const double d = (double)(float)m.kn.s[j] - m.kn.s[j];
+    double b[4];
+    b[0] = a[0] + d * (a[1] + d * (a[2] + d * a[3]));
+    b[1] = a[1] + d * (2.0 * a[2] + 3.0 * d * a[3]);
+    b[2] = a[2] + 3.0 * d * a[3];
+    b[3] = a[3];
+    float* f = coef32 + j * 16 + s * 8;
+    for (int k = 0; k < 4; ++k) {
+      const float hi = (float)b[k];
+      f[k] = hi;
+      f[4 + k] = (float)(b[k] - (double)hi);
+    }
   }
   for (int k = threadIdx.x; k < 2 * n_res; k += blockDim.x) coef[8 * nseg + k] = params[k];
+  // FP32 form: c'_r = c_r cscale_r as hi/lo pairs
+  for (int k = threadIdx.x; k < 2 * n_res; k += blockDim.x) {
+    const double v = params[k] * m.cscale[k >> 1];
+    const float hi = (float)v;
+    coef32[16 * nseg + 2 * k] = hi;
+    coef32[16 * nseg + 2 * k + 1] = (float)(v - (double)hi);
+  }
 }
 
 void launch_prepare(const Model& m, const double* params, const double* lu, double* coef,
-                    cudaStream_t st) {
-  prepare_kernel<<<1, 64, 0, st>>>(m.n_res, m.kn.n, params, lu, coef);
+                    float* coef32, cudaStream_t st) {
+  prepare_kernel<<<1, 64, 0, st>>>(m, params, lu, coef, coef32);
 }
 
 }  // namespace mipwa
