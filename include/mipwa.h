@@ -158,6 +158,37 @@ int mipwa_inside(mipwa_ctx* ctx, const void* d_s12s13, int64_t n, int dtype,
 int mipwa_set_timing(mipwa_ctx* ctx, int on);
 int mipwa_kernel_time(mipwa_ctx* ctx, double* ms, int64_t* n_launches);
 
+/* Allocation-free NLL + gradient, for callers that cannot allocate device
+ * memory: code embedded in a framework that owns the device heap, a serving
+ * process whose memory is sized once at start-up, or a plug-in whose host
+ * forbids allocation after initialisation. (The paper has no counterpart; it
+ * is a deployment entry point, not part of the method.)
+ *
+ * Computes the same [NLL, dNLL/dparams] as mipwa_nll_grad without a context:
+ * the model comes as arguments (same meaning and rules as set_masses and
+ * set_model), the events as DEVICE pointers (d_data: n_data >= 0 pairs,
+ * d_norm: n_norm >= 1 pairs, both of type `dtype`, all inside the Dalitz plot
+ * or MIPWA_EOUTSIDE), params as P host doubles, and the result is written to
+ * the DEVICE buffer d_out (at least 1 + P doubles). Work is queued on
+ * `stream` (NULL: legacy default stream); the call blocks until it is done.
+ * Events are used in the caller's order (not regrouped by spline cell).
+ *
+ * It calls no allocator: every intermediate buffer lives in one fixed
+ * file-scope device array of about 2.5 MB (at most 608 blocks, N <= 64 knots,
+ * R <= 4 resonances), which every GPU that loads the library holds until the
+ * process exits. The first call on a device looks up that array's address;
+ * make it before any CUDA stream capture. All calls share the array, so calls
+ * that overlap on the GPU (other host threads, other streams) race; the
+ * counters that must start at zero are cleared on every call. Returns
+ * MIPWA_EINVAL for sizes beyond these limits or bad arguments, MIPWA_ENONPOS
+ * when |A|^2 <= 0 for a data event or the integral is not positive, and
+ * MIPWA_ECUDA (with a line on stderr) if a CUDA call fails. */
+int mipwa_nll_grad_noalloc(int device, int compute_mode, double mD, double m1, double m2,
+                           const mipwa_resonance* res, int n_res, const double* knots,
+                           int n_knots, double r_res, double r_D, const void* d_data,
+                           int64_t n_data, const void* d_norm, int64_t n_norm, int dtype,
+                           const double* params, double* d_out, void* stream);
+
 /* One-line description of the last failure on this context ("" if none). */
 const char* mipwa_last_error(const mipwa_ctx* ctx);
 

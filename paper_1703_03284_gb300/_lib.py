@@ -43,6 +43,8 @@ SIGNATURES = [
     ("mipwa_nll_grad", _i, [_vp, _pd, _pd, _pd]),
     ("mipwa_amp2", _i, [_vp, _pd, _vp, _i64, _i, _vp]),
     ("mipwa_inside", _i, [_vp, _vp, _i64, _i, _vp]),
+    ("mipwa_nll_grad_noalloc", _i, [_i, _i, _d, _d, _d, ctypes.POINTER(Resonance), _i, _pd, _i,
+                                    _d, _d, _vp, _i64, _vp, _i64, _i, _pd, _vp, _vp]),
     ("mipwa_set_timing", _i, [_vp, _i]),
     ("mipwa_kernel_time", _i, [_vp, _pd, _pi64]),
     ("mipwa_last_error", ctypes.c_char_p, [_vp]),

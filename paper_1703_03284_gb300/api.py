@@ -207,3 +207,38 @@ class Likelihood:
 
     def launch_count(self) -> int:
         return int(self._lib.mipwa_launch_count(self._h))
+
+
+def nll_grad_noalloc(spec, params, data, norm, compute_mode: int = F64, device: int = 0):
+    """mipwa_nll_grad_noalloc through the C ABI: no context and no device
+    allocation inside the library. `data` and `norm` are CUDA tensors (n, 2) of
+    one dtype; returns (NLL, gradient) read back from a caller-owned buffer."""
+    import torch
+    lib = _lib.load()
+    if not (isinstance(data, torch.Tensor) and data.is_cuda and isinstance(norm, torch.Tensor)
+            and norm.is_cuda and data.dtype == norm.dtype):
+        raise ValueError("data and norm must be CUDA tensors of one dtype")
+    d_ptr, nd, code, _, kd = _event_buffer(data)
+    n_ptr, nn, code_n, _, kn = _event_buffer(norm)
+    res = (_lib.Resonance * max(len(spec.resonances), 1))()
+    for i, (mass, width, spin) in enumerate(spec.resonances):
+        res[i] = _lib.Resonance(float(mass), float(width), int(spin))
+    knots = np.ascontiguousarray(spec.knots, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    P = 2 * len(spec.resonances) + 2 * len(knots)
+    if p.shape != (P,):
+        raise ValueError(f"expected {P} parameters")
+    out = torch.empty(1 + P, dtype=torch.float64, device=data.device)
+    stream = torch.cuda.current_stream(data.device).cuda_stream
+    pd = ctypes.POINTER(ctypes.c_double)
+    rc = lib.mipwa_nll_grad_noalloc(
+        int(device), int(compute_mode), float(spec.mD), float(spec.m1), float(spec.m2), res,
+        len(spec.resonances), knots.ctypes.data_as(pd), len(knots), float(spec.r_res),
+        float(spec.r_D), ctypes.c_void_p(d_ptr), nd, ctypes.c_void_p(n_ptr), nn, code,
+        p.ctypes.data_as(pd), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
+    del kd, kn
+    if rc != _lib.OK:
+        raise MipwaError(rc, "mipwa_nll_grad_noalloc failed")
+    o = out.cpu().numpy()
+    return float(o[0]), o[1:].copy()
+

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/mipwa.h"
+#include "mipwa_host.h"
 #include "mipwa_kernels.cuh"
 
 using namespace mipwa;
@@ -91,6 +92,10 @@ double kallen_sqrt(double x, double a, double b) {
   return std::sqrt(l);
 }
 
+}  // namespace
+
+namespace mipwa {
+
 // Fill the FP64 and FP32 constant blocks from masses, resonances and radii.
 void derive(Model& m, const mipwa_resonance* res, int n_res, double r_res, double r_D) {
   const double M = m.mD, m1 = m.m1, m2 = m.m2, m3 = m.m2;
@@ -163,6 +168,10 @@ void factor_spline(const Knots& kn, std::vector<double>& lu) {
     prev_dia = dd;
   }
 }
+
+}  // namespace mipwa
+
+namespace {
 
 int ensure(mipwa_ctx* c, void** p, size_t* cap, size_t bytes) {
   if (*cap >= bytes && *p) return MIPWA_OK;
