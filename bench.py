@@ -44,9 +44,10 @@ FLOPS_PER_EVENT_GRAD = 291
 PEAK_FP32_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25
 # DRAM bytes (read + write) per launch of the fused FP32 NLL+gradient kernel
-# from one ncu capture (profiles/eval_kernel_f32_grad.txt), scaled to this
-# workload by events processed; None until captured for the current kernel.
-TRAFFIC_PER_LAUNCH = None
+# from one ncu capture on 2e7 + 2e7 events (profiles/eval_kernel_f32_grad_pipipi_n40.md),
+# scaled to this workload by the events processed (x5); None once the kernel
+# has changed since the capture.
+TRAFFIC_PER_LAUNCH = 1.620e9
 
 
 def parse():
