@@ -43,6 +43,20 @@ FLOPS_PER_EVENT_GRAD = 291
 #   FP32: 128 lanes x 2 flop x 152 x 2.07 GHz;  FP64: 1.25 TFLOP/s (GB300 nominal).
 PEAK_FP32_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25
+# Cached basis: the Breit-Wigner part (kinematics 24, Zemach 18, BW terms 86,
+# symmetrisation 4 flops) is read from memory instead.
+FLOPS_PER_EVENT_GRAD_CACHED = FLOPS_PER_EVENT_GRAD - 132
+
+
+def _measured_hbm_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0  # fallback figure for a GB300
+
+
+HBM_GBS = _measured_hbm_gbs()
 # DRAM bytes (read + write) per launch of the fused FP32 NLL+gradient kernel
 # from one ncu capture on 2e7 + 2e7 events (profiles/eval_kernel_f32_grad_pipipi_n40.md),
 # scaled to this workload by the events processed (x5); None once the kernel
@@ -60,6 +74,7 @@ def parse():
                     help="data events (= normalisation events)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cached-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -312,6 +327,37 @@ def run(args, world, rank, local, stream):
                              "traffic": None, "kernel": "eval_kernel<double,float2,grad>",
                              "peak_note": "GB300 nominal FP64, not measured"}}
 
+    # ---- FP32-mixed with the cached Breit-Wigner basis (8 + 8R bytes per event)
+    cached = None
+    if args.cached_steps > 0:
+        lik.enable_basis_cache(True)
+        lik.nll_grad(params)  # builds the cache
+        lik.nll_grad(params)
+        lik.set_timing(True)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.cached_steps):
+            lik.nll_grad(params)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        tc = max_over_ranks(c0.elapsed_time(c1), world)
+        kmsc, knc = lik.kernel_time()
+        lik.set_timing(False)
+        lik.enable_basis_cache(False)
+        k_sc = kmsc / knc / 1e3
+        bytes_ev = 8 + 8 * spec.n_res
+        achc = FLOPS_PER_EVENT_GRAD_CACHED * events / k_sc / 1e12
+        hbm = bytes_ev * events / k_sc / 1e9
+        cached = {"value": world * events * args.cached_steps / (tc / 1e3), "unit": "events/s",
+                  "ms_per_step": tc / args.cached_steps, "steps": args.cached_steps,
+                  "bytes_per_event": bytes_ev,
+                  "roofline": {"bound": "alu", "achieved": achc, "peak": PEAK_FP32_TFLOPS,
+                               "unit": "TFLOP/s", "frac": achc / PEAK_FP32_TFLOPS,
+                               "hbm_gbs": hbm, "hbm_frac_of_measured": hbm / HBM_GBS,
+                               "traffic": None,
+                               "kernel": "eval_kernel<float,float2,grad,cached>"}}
+
     # ---- end to end from pinned host buffers through the C ABI
     e2e = None
     if args.e2e_steps > 0:
@@ -349,7 +395,8 @@ def run(args, world, rank, local, stream):
             "config": {"workload": WORKLOAD, "n_data": n, "n_norm": n,
                        "l2": "inputs (1.6 GB) larger than L2 (129 MB); no flush needed",
                        "parallelism": f"replicas x{world} (no collective)"},
-            "roofline": roofline, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roofline, "fp64_plain": fp64, "fp32_cached_basis": cached, "e2e": e2e,
+            "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)
 

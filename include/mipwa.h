@@ -128,6 +128,16 @@ int mipwa_set_events(mipwa_ctx* ctx, const void* s12s13, int64_t n, int dtype,
 int mipwa_set_norm_sample(mipwa_ctx* ctx, const void* s12s13, int64_t n, int dtype,
                           int on_device, int64_t* n_outside);
 
+/* Cached per-event basis (on != 0): with the Breit-Wigner masses, widths and
+ * radii fixed, the Bose-symmetrised terms A_r(s12,s13) + A_r(s13,s12) of Eq. 1
+ * depend on the event only, not on the fit parameters c_r, a_k, phi_k (Sec. 2).
+ * The context then stores them once per event (8 R bytes per event in
+ * MIPWA_F32 mode, 16 R in MIPWA_F64) and each evaluation reads them instead of
+ * recomputing kinematics, barrier factors and propagators. The cache is
+ * rebuilt on the next evaluation after set_masses, set_model, set_events,
+ * set_norm_sample or set_compute_mode. on = 0 frees it. */
+int mipwa_enable_basis_cache(mipwa_ctx* ctx, int on);
+
 /* P = 2 n_res + 2 n_knots of the current model, or -1 without a model. */
 int mipwa_num_params(const mipwa_ctx* ctx);
 

@@ -38,6 +38,7 @@ SIGNATURES = [
     ("mipwa_set_model", _i, [_vp, ctypes.POINTER(Resonance), _i, _pd, _i, _d, _d]),
     ("mipwa_set_events", _i, [_vp, _vp, _i64, _i, _i, _pi64]),
     ("mipwa_set_norm_sample", _i, [_vp, _vp, _i64, _i, _i, _pi64]),
+    ("mipwa_enable_basis_cache", _i, [_vp, _i]),
     ("mipwa_num_params", _i, [_vp]),
     ("mipwa_nll", _i, [_vp, _pd, _pd]),
     ("mipwa_nll_grad", _i, [_vp, _pd, _pd, _pd]),

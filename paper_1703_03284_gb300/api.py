@@ -133,6 +133,9 @@ class Likelihood:
     def set_norm_sample(self, x):
         self._set(self._lib.mipwa_set_norm_sample, x)
 
+    def enable_basis_cache(self, on: bool = True):
+        self._check(self._lib.mipwa_enable_basis_cache(self._h, int(bool(on))))
+
     def num_params(self) -> int:
         return int(self._lib.mipwa_num_params(self._h))
 

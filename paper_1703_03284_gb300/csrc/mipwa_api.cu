@@ -49,7 +49,11 @@ struct mipwa_ctx {
     int dtype = MIPWA_F64;
     bool set = false;
     bool sorted = false;  // grouped by spline cell of the current knots
+    void* basis = nullptr;  // cached B_r per event (resonance-major)
+    size_t basis_cap = 0;
+    bool basis_valid = false;
   } data, norm;
+  bool basis_on = false;
   int64_t launches = 0;
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -222,6 +226,24 @@ int sort_into(mipwa_ctx* c, const void* src, int64_t n, int dtype, void* dst) {
 
 bool sortable(int64_t n) { return n > 1 && n < (int64_t)0x7fffffff; }
 
+void invalidate_basis(mipwa_ctx* c) { c->data.basis_valid = c->norm.basis_valid = false; }
+
+// (Re)build the cached Breit-Wigner basis of a sample for the current model
+// and compute mode.
+int build_basis(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
+  if (smp.basis_valid || smp.n == 0) return MIPWA_OK;
+  const bool f32 = c->mode == MIPWA_F32;
+  const size_t bytes =
+      (size_t)smp.n * (size_t)(c->model.n_res > 0 ? c->model.n_res : 1) * (f32 ? 8 : 16);
+  int rc = ensure(c, &smp.basis, &smp.basis_cap, bytes);
+  if (rc) return rc;
+  CK(c, launch_basis(f32, smp.dtype == MIPWA_F32, c->model, smp.cur, smp.n, smp.basis,
+                     grid_for(c, smp.n), c->stream));
+  c->launches++;
+  smp.basis_valid = true;
+  return MIPWA_OK;
+}
+
 int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n, int dtype,
                int on_device, int64_t* n_outside, bool allow_empty) {
   int rc = check_ctx(c);
@@ -272,6 +294,7 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
   smp.n = n;
   smp.dtype = dtype;
   smp.set = true;
+  smp.basis_valid = false;
   return MIPWA_OK;
 }
 
@@ -287,6 +310,7 @@ int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
   std::swap(smp.cur, smp.spare);
   std::swap(smp.cur_cap, smp.spare_cap);
   smp.sorted = true;
+  smp.basis_valid = false;
   return MIPWA_OK;
 }
 
@@ -326,6 +350,12 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   rc = ensure(c, (void**)&c->d_partials, &c->partials_cap, (size_t)grid * W * sizeof(double));
   if (rc) return rc;
 
+  if (c->basis_on) {
+    rc = build_basis(c, c->data);
+    if (rc) return rc;
+    rc = build_basis(c, c->norm);
+    if (rc) return rc;
+  }
   std::memcpy(c->h_stage, params, P * sizeof(double));
   CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, P * sizeof(double), cudaMemcpyHostToDevice,
                         c->stream));
@@ -347,6 +377,8 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   a.counter = c->d_counter;
   a.out = c->d_out;
   a.flags = c->d_flags;
+  a.basis_data = c->basis_on ? c->data.basis : nullptr;
+  a.basis_norm = c->basis_on ? c->norm.basis : nullptr;
   a.model = c->model;
   if (c->timing) CK(c, cudaEventRecord(c->ev0, c->stream));
   CK(c, launch_eval(f32, ev32, want_grad, a, grid, c->stream));
@@ -424,7 +456,8 @@ void mipwa_destroy(mipwa_ctx* c) {
   for (void* p : {(void*)c->d_lu, (void*)c->d_params, (void*)c->d_coef, (void*)c->d_coef32,
                   (void*)c->d_out,
                   (void*)c->d_flags, (void*)c->d_counter, (void*)c->d_count,
-                  (void*)c->d_partials, (void*)c->d_sortwork, c->data.cur, c->data.spare, c->norm.cur,
+                  (void*)c->d_partials, (void*)c->d_sortwork, c->data.basis, c->norm.basis,
+                  c->data.cur, c->data.spare, c->norm.cur,
                   c->norm.spare})
     if (p) cudaFree(p);
   if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -447,6 +480,7 @@ int mipwa_set_compute_mode(mipwa_ctx* c, int mode) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (mode != MIPWA_F64 && mode != MIPWA_F32) return fail(c, MIPWA_EINVAL, "bad compute mode");
+  if (mode != c->mode) invalidate_basis(c);
   c->mode = mode;
   return MIPWA_OK;
 }
@@ -462,6 +496,7 @@ int mipwa_set_masses(mipwa_ctx* c, double mD, double m1, double m2) {
   c->model.m2 = m2;
   c->have_masses = true;
   c->have_model = false;
+  invalidate_basis(c);
   c->n_params = -1;
   c->data.set = c->norm.set = false;
   c->data.n = c->norm.n = 0;
@@ -514,6 +549,7 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   c->model = m;
   c->n_params = 2 * n_res + 2 * n_knots;
   c->have_model = true;
+  invalidate_basis(c);
   rc = resort(c, c->data);
   if (rc) return rc;
   return resort(c, c->norm);
@@ -578,6 +614,21 @@ int mipwa_inside(mipwa_ctx* c, const void* ev, int64_t n, int dtype, uint8_t* ou
                       c->stream));
   c->launches++;
   CK(c, cudaStreamSynchronize(c->stream));
+  return MIPWA_OK;
+}
+
+int mipwa_enable_basis_cache(mipwa_ctx* c, int on) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->basis_on = on != 0;
+  if (!c->basis_on) {
+    for (mipwa_ctx::Sample* smp : {&c->data, &c->norm}) {
+      if (smp->basis) cudaFree(smp->basis);
+      smp->basis = nullptr;
+      smp->basis_cap = 0;
+    }
+  }
+  invalidate_basis(c);
   return MIPWA_OK;
 }
 

@@ -10,6 +10,7 @@
 // writes -2 ln L and its gradient (the adjoint of the spline solve included).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -17,6 +18,22 @@
 #include "mipwa_kernels.cuh"
 
 namespace mipwa {
+
+// Compile-time model signature of the FP32 kernels: 0 = read the resonance
+// count and spins from the model at run time; otherwise one decimal digit per
+// resonance, digit = L + 1 (23: a P-wave and a D-wave).
+__host__ __device__ constexpr int sig_count(int sig) {
+  int n = 0;
+  for (; sig > 0; sig /= 10) ++n;
+  return n;
+}
+// spin of resonance r (digit r counted from the most significant one)
+__host__ __device__ constexpr int sig_L(int sig, int r) {
+  for (int k = sig_count(sig) - 1 - r; k > 0; --k) sig /= 10;
+  return sig % 10 - 1;
+}
+constexpr int kSigPD = 23;
+static_assert(sig_count(kSigPD) == 2 && sig_L(kSigPD, 0) == 1 && sig_L(kSigPD, 1) == 2, "sig");
 
 // Per-thread running sums: plain FP64, or Kahan-compensated FP32.
 template <typename T>
@@ -107,19 +124,16 @@ struct SwavePart {
   T t, a, cs, sn;
 };
 
-// Forward amplitude of one event, FP64 form. Fills the Bose-symmetrised
-// Breit-Wigner basis B[r] and the S-wave pieces of both channels.
-__device__ __forceinline__ Cplx<double> amplitude(const Model& m, const EvalSmem<double>& sm,
-                                                  double s12, double s13, Cplx<double>* B,
-                                                  SwavePart<double>& w12,
-                                                  SwavePart<double>& w13) {
+// ---------------------------------------------------------------- FP64 form
+// Bose-symmetrised Breit-Wigner basis B_r = A_r(s12,s13) + A_r(s13,s12).
+__device__ __forceinline__ void bw_basis(const Model& m, double s12, double s13,
+                                         Cplx<double>* B) {
   const ConstsD& c = m.cd;
   const ChanD k12 = channel_d(c, s12);
   const ChanD k13 = channel_d(c, s13);
   double z1a, z2a, z1b, z2b;
   zemach_d(c, k12, s13, z1a, z2a);
   zemach_d(c, k13, s12, z1b, z2b);
-  Cplx<double> A{0.0, 0.0};
 #pragma unroll
   for (int r = 0; r < kMaxRes; ++r) {
     if (r < m.n_res) {
@@ -127,27 +141,39 @@ __device__ __forceinline__ Cplx<double> amplitude(const Model& m, const EvalSmem
       const Cplx<double> v = bw_d(c, r, k13, z1b, z2b);
       B[r].re = u.re + v.re;
       B[r].im = u.im + v.im;
+    }
+  }
+}
+
+// A = sum_r c_r B_r
+template <int NR>
+__device__ __forceinline__ Cplx<double> combine(const Model& m, const EvalSmem<double>& sm,
+                                                const Cplx<double>* B) {
+  Cplx<double> A{0.0, 0.0};
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r < m.n_res) {
       A.re += sm.cre[r] * B[r].re - sm.cim[r] * B[r].im;
       A.im += sm.cre[r] * B[r].im + sm.cim[r] * B[r].re;
     }
   }
-  SwavePart<double>* ws[2] = {&w12, &w13};
-  const double ss[2] = {s12, s13};
-#pragma unroll
-  for (int ch = 0; ch < 2; ++ch) {
-    SwavePart<double>& w = *ws[ch];
-    w.j = segment_of(m.kn, sm.knot, ss[ch]);
-    w.t = ss[ch] - sm.knot[w.j];
-    const double* a = &sm.coef[w.j * 8];
-    w.a = ((a[3] * w.t + a[2]) * w.t + a[1]) * w.t + a[0];
-    const double ph = ((a[7] * w.t + a[6]) * w.t + a[5]) * w.t + a[4];
-    sincos(ph, &w.sn, &w.cs);
-    A.re += w.a * w.cs;
-    A.im += w.a * w.sn;
-  }
   return A;
 }
 
+// A += a(s) e^{i phi(s)} for one channel.
+__device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<double>& sm, double s,
+                                          SwavePart<double>& w, Cplx<double>& A) {
+  w.j = segment_of(m.kn, sm.knot, s);
+  w.t = s - sm.knot[w.j];
+  const double* a = &sm.coef[w.j * 8];
+  w.a = ((a[3] * w.t + a[2]) * w.t + a[1]) * w.t + a[0];
+  const double ph = ((a[7] * w.t + a[6]) * w.t + a[5]) * w.t + a[4];
+  sincos(ph, &w.sn, &w.cs);
+  A.re += w.a * w.cs;
+  A.im += w.a * w.sn;
+}
+
+// ---------------------------------------------------------------- FP32 form
 // FP32 form: cubic value as an exact pair hi + lo: the hi-coefficient Horner
 // tail t (a1 + a2 t + a3 t^2) plus a0 by TwoSum, the lo-coefficient Horner
 // added to the low part.
@@ -159,9 +185,9 @@ __device__ __forceinline__ F2 cubic_hl(const float4 hi, const float4 lo, float t
   return v;
 }
 
-__device__ __forceinline__ Cplx<float> amplitude(const Model& m, const EvalSmem<float>& sm,
-                                                 float s12, float s13, Cplx<float>* B,
-                                                 SwavePart<float>& w12, SwavePart<float>& w13) {
+// B_r / cscale_r for the FP32 form (SIG: compile-time resonance spins, or 0).
+template <int SIG>
+__device__ __forceinline__ void bw_basis(const Model& m, float s12, float s13, Cplx<float>* B) {
   const ConstsF& c = m.cf;
   const ChanF k12 = channel_f(c, s12);
   const ChanF k13 = channel_f(c, s13);
@@ -169,33 +195,67 @@ __device__ __forceinline__ Cplx<float> amplitude(const Model& m, const EvalSmem<
   float z2a, z2b;
   zemach_f(c, k12, s13, z1a, z2a);
   zemach_f(c, k13, s12, z1b, z2b);
-  Cplx<float> A{0.0f, 0.0f};
+  constexpr int NR = SIG ? sig_count(SIG) : kMaxRes;
 #pragma unroll
-  for (int r = 0; r < kMaxRes; ++r) {
-    if (r < m.n_res) {
-      const Cplx<float> u = bw_f(c, r, k12, z1a, z2a);
-      const Cplx<float> v = bw_f(c, r, k13, z1b, z2b);
+  for (int r = 0; r < NR; ++r) {
+    if (SIG || r < m.n_res) {
+      const int L = SIG ? sig_L(SIG, r) : c.L[r];
+      const Cplx<float> u = bw_f(c, r, L, k12, z1a, z2a);
+      const Cplx<float> v = bw_f(c, r, L, k13, z1b, z2b);
       B[r].re = u.re + v.re;
       B[r].im = u.im + v.im;
+    }
+  }
+}
+
+template <int NR>
+__device__ __forceinline__ Cplx<float> combine(const Model& m, const EvalSmem<float>& sm,
+                                               const Cplx<float>* B) {
+  Cplx<float> A{0.0f, 0.0f};
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r < m.n_res) {
       A.re += mul_hl(sm.cre[r], sm.cre_lo[r], B[r].re) - mul_hl(sm.cim[r], sm.cim_lo[r], B[r].im);
       A.im += mul_hl(sm.cre[r], sm.cre_lo[r], B[r].im) + mul_hl(sm.cim[r], sm.cim_lo[r], B[r].re);
     }
   }
-  SwavePart<float>* ws[2] = {&w12, &w13};
-  const float ss[2] = {s12, s13};
+  return A;
+}
+
+__device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<float>& sm, float s,
+                                          SwavePart<float>& w, Cplx<float>& A) {
+  w.j = segment_of(m.kn, sm.knot, s);
+  w.t = __fsub_rn(s, sm.knot[w.j]);  // exact (Sterbenz) on the knot grids used here
+  const float4* c4 = reinterpret_cast<const float4*>(&sm.coef[w.j * 16]);
+  const F2 a = cubic_hl(c4[0], c4[1], w.t);
+  const F2 ph = cubic_hl(c4[2], c4[3], w.t);
+  sincos_cw(ph.hi, ph.lo, &w.sn, &w.cs);
+  w.a = a.hi;
+  A.re += mul_hl(a.hi, a.lo, w.cs);
+  A.im += mul_hl(a.hi, a.lo, w.sn);
+}
+
+// ------------------------------------------------------ whole amplitude
+// Forward amplitude of one event: fills the Bose-symmetrised Breit-Wigner
+// basis B[r] (FP32 form: B_r / cscale_r) and the S-wave pieces of both
+// channels. With a cached basis, B is read instead of computed.
+template <typename T, int SIG, bool CACHED>
+__device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& sm, T s12, T s13,
+                                             const Cplx<T>* cached, int64_t i, int64_t n,
+                                             Cplx<T>* B, SwavePart<T>& w12, SwavePart<T>& w13) {
+  constexpr int NR = SIG ? sig_count(SIG) : kMaxRes;
+  if constexpr (CACHED) {
 #pragma unroll
-  for (int ch = 0; ch < 2; ++ch) {
-    SwavePart<float>& w = *ws[ch];
-    w.j = segment_of(m.kn, sm.knot, ss[ch]);
-    w.t = __fsub_rn(ss[ch], sm.knot[w.j]);  // exact (Sterbenz) on the knot grids used here
-    const float4* c4 = reinterpret_cast<const float4*>(&sm.coef[w.j * 16]);
-    const F2 a = cubic_hl(c4[0], c4[1], w.t);
-    const F2 ph = cubic_hl(c4[2], c4[3], w.t);
-    sincos_cw(ph.hi, ph.lo, &w.sn, &w.cs);
-    w.a = a.hi;
-    A.re += mul_hl(a.hi, a.lo, w.cs);
-    A.im += mul_hl(a.hi, a.lo, w.sn);
+    for (int r = 0; r < NR; ++r)
+      if (r < m.n_res) B[r] = cached[(int64_t)r * n + i];
+  } else if constexpr (std::is_same<T, float>::value) {
+    bw_basis<SIG>(m, s12, s13, B);
+  } else {
+    bw_basis(m, s12, s13, B);
   }
+  Cplx<T> A = combine<NR>(m, sm, B);
+  swave_add(m, sm, s12, w12, A);
+  swave_add(m, sm, s13, w13, A);
   return A;
 }
 
@@ -352,7 +412,7 @@ __device__ void finalize(EvalSmem<T>& sm, const EvalArgs& a) {
   if (threadIdx.x == 0) *a.counter = 0u;
 }
 
-template <typename T, typename EvT, bool GRAD>
+template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED>
 __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
   __shared__ EvalSmem<T> sm;
   const Model& m = a.model;
@@ -371,6 +431,8 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
   const int nb = is_data ? a.nb_data : a.nb_norm;
   const int b = is_data ? (int)blockIdx.x : (int)blockIdx.x - a.nb_data;
   const EvT* ev = reinterpret_cast<const EvT*>(is_data ? a.data : a.norm);
+  const Cplx<T>* cached =
+      reinterpret_cast<const Cplx<T>*>(is_data ? a.basis_data : a.basis_norm);
   const int64_t stride = (int64_t)nb * kThreads;
 
   Acc<T> sum;
@@ -390,7 +452,7 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
     if (i < n) {
       const EvT e = ev[i];
       const T s12 = (T)e.x, s13 = (T)e.y;
-      A = amplitude(m, sm, s12, s13, B, w12, w13);
+      A = amplitude<T, SIG, CACHED>(m, sm, s12, s13, cached, i, n, B, w12, w13);
       const T A2 = A.re * A.re + A.im * A.im;
       if (is_data) {
         ok = A2 > T(0) && isfinite(A2);
@@ -402,7 +464,7 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
           } else {
             sum.add(log(A2));
           }
-          wt = T(1) / A2;
+          if constexpr (std::is_same<T, float>::value) wt = rcp_nr(A2); else wt = T(1) / A2;
         }
       } else {
         ok = isfinite(A2);
@@ -413,9 +475,10 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
     if constexpr (GRAD) {
       T v[16];
       if (ok) {
+        constexpr int NRg = SIG ? sig_count(SIG) : kMaxRes;
 #pragma unroll
-        for (int r = 0; r < kMaxRes; ++r) {
-          if (r < R) {
+        for (int r = 0; r < NRg; ++r) {
+          if (SIG || r < R) {
             gc[2 * r] += T(2) * wt * (A.re * B[r].re + A.im * B[r].im);
             gc[2 * r + 1] += T(2) * wt * (A.im * B[r].re - A.re * B[r].im);
           }
@@ -496,10 +559,28 @@ __global__ void __launch_bounds__(kThreads) amp2_kernel(const Model m, const dou
     if (inside_plot(m, (double)e.x, (double)e.y)) {
       Cplx<T> B[kMaxRes];
       SwavePart<T> w12, w13;
-      const Cplx<T> A = amplitude(m, sm, (T)e.x, (T)e.y, B, w12, w13);
+      const Cplx<T> A =
+          amplitude<T, 0, false>(m, sm, (T)e.x, (T)e.y, nullptr, 0, 0, B, w12, w13);
       v = (double)(A.re * A.re + A.im * A.im);
     }
     out[i] = v;
+  }
+}
+
+// ------------------------------------------------- cached Breit-Wigner basis
+// B_r for every event of a sample, stored resonance-major: out[r * n + i].
+template <typename T, typename EvT, int SIG>
+__global__ void __launch_bounds__(kThreads) basis_kernel(const Model m, const EvT* ev, int64_t n,
+                                                         Cplx<T>* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const EvT e = ev[i];
+    Cplx<T> B[kMaxRes];
+    if constexpr (std::is_same<T, float>::value) bw_basis<SIG>(m, (T)e.x, (T)e.y, B);
+    else bw_basis(m, (T)e.x, (T)e.y, B);
+#pragma unroll
+    for (int r = 0; r < kMaxRes; ++r)
+      if (r < m.n_res) out[(int64_t)r * n + i] = B[r];
   }
 }
 
@@ -520,40 +601,87 @@ __global__ void inside_kernel(const Model m, const EvT* ev, int64_t n, uint8_t* 
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T, typename EvT, bool GRAD>
+template <typename T, typename EvT, bool GRAD, int SIG = 0, bool CACHED = false>
 static cudaError_t run_eval(const EvalArgs& a, int grid, cudaStream_t st) {
-  eval_kernel<T, EvT, GRAD><<<grid, kThreads, 0, st>>>(a);
+  eval_kernel<T, EvT, GRAD, SIG, CACHED><<<grid, kThreads, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+// The model's compile-time signature, if a specialised FP32 kernel exists.
+static int model_sig(const Model& m) {
+  if (m.n_res == 2 && m.cf.L[0] == 1 && m.cf.L[1] == 2) return kSigPD;
+  return 0;
+}
+
+template <typename T, typename EvT>
+static cudaError_t dispatch_eval(bool grad, bool cached, bool pd, const EvalArgs& a, int grid,
+                                 cudaStream_t st) {
+  if (cached) return grad ? run_eval<T, EvT, true, 0, true>(a, grid, st)
+                          : run_eval<T, EvT, false, 0, true>(a, grid, st);
+  if constexpr (std::is_same<T, float>::value) {
+    if (pd) return grad ? run_eval<T, EvT, true, kSigPD>(a, grid, st)
+                        : run_eval<T, EvT, false, kSigPD>(a, grid, st);
+  }
+  return grad ? run_eval<T, EvT, true>(a, grid, st) : run_eval<T, EvT, false>(a, grid, st);
 }
 
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t st) {
+  const bool cached = a.basis_norm != nullptr;
+  const bool pd = model_sig(a.model) == kSigPD;
   if (compute_f32) {
-    if (ev_f32) return grad ? run_eval<float, float2, true>(a, grid, st)
-                            : run_eval<float, float2, false>(a, grid, st);
-    return grad ? run_eval<float, double2, true>(a, grid, st)
-                : run_eval<float, double2, false>(a, grid, st);
+    if (ev_f32) return dispatch_eval<float, float2>(grad, cached, pd, a, grid, st);
+    return dispatch_eval<float, double2>(grad, cached, pd, a, grid, st);
   }
-  if (ev_f32) return grad ? run_eval<double, float2, true>(a, grid, st)
-                          : run_eval<double, float2, false>(a, grid, st);
-  return grad ? run_eval<double, double2, true>(a, grid, st)
-              : run_eval<double, double2, false>(a, grid, st);
+  if (ev_f32) return dispatch_eval<double, float2>(grad, cached, pd, a, grid, st);
+  return dispatch_eval<double, double2>(grad, cached, pd, a, grid, st);
 }
 
-template <typename T, typename EvT, bool GRAD>
+cudaError_t launch_basis(int compute_f32, int ev_f32, const Model& m, const void* ev, int64_t n,
+                         void* out, int grid, cudaStream_t st) {
+  const bool pd = model_sig(m) == kSigPD;
+  if (compute_f32) {
+    if (ev_f32) {
+      if (pd) basis_kernel<float, float2, kSigPD><<<grid, kThreads, 0, st>>>(m, (const float2*)ev, n, (Cplx<float>*)out);
+      else basis_kernel<float, float2, 0><<<grid, kThreads, 0, st>>>(m, (const float2*)ev, n, (Cplx<float>*)out);
+    } else {
+      if (pd) basis_kernel<float, double2, kSigPD><<<grid, kThreads, 0, st>>>(m, (const double2*)ev, n, (Cplx<float>*)out);
+      else basis_kernel<float, double2, 0><<<grid, kThreads, 0, st>>>(m, (const double2*)ev, n, (Cplx<float>*)out);
+    }
+  } else {
+    if (ev_f32) basis_kernel<double, float2, 0><<<grid, kThreads, 0, st>>>(m, (const float2*)ev, n, (Cplx<double>*)out);
+    else basis_kernel<double, double2, 0><<<grid, kThreads, 0, st>>>(m, (const double2*)ev, n, (Cplx<double>*)out);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, typename EvT, bool GRAD, int SIG = 0, bool CACHED = false>
 static int occ() {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<T, EvT, GRAD>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<T, EvT, GRAD, SIG, CACHED>,
+                                                kThreads, 0);
   return nb > 0 ? nb : 1;
 }
 
 int eval_blocks_per_sm(int compute_f32, int ev_f32, bool grad) {
+  // the generic, specialised and cached kernels share one grid: take the
+  // smallest occupancy of the variants
   if (compute_f32) {
-    if (ev_f32) return grad ? occ<float, float2, true>() : occ<float, float2, false>();
-    return grad ? occ<float, double2, true>() : occ<float, double2, false>();
+    if (ev_f32)
+      return grad ? std::min({occ<float, float2, true>(), occ<float, float2, true, kSigPD>(),
+                              occ<float, float2, true, 0, true>()})
+                  : std::min({occ<float, float2, false>(), occ<float, float2, false, kSigPD>(),
+                              occ<float, float2, false, 0, true>()});
+    return grad ? std::min({occ<float, double2, true>(), occ<float, double2, true, kSigPD>(),
+                            occ<float, double2, true, 0, true>()})
+                : std::min({occ<float, double2, false>(), occ<float, double2, false, kSigPD>(),
+                            occ<float, double2, false, 0, true>()});
   }
-  if (ev_f32) return grad ? occ<double, float2, true>() : occ<double, float2, false>();
-  return grad ? occ<double, double2, true>() : occ<double, double2, false>();
+  if (ev_f32)
+    return grad ? std::min(occ<double, float2, true>(), occ<double, float2, true, 0, true>())
+                : std::min(occ<double, float2, false>(), occ<double, float2, false, 0, true>());
+  return grad ? std::min(occ<double, double2, true>(), occ<double, double2, true, 0, true>())
+              : std::min(occ<double, double2, false>(), occ<double, double2, false, 0, true>());
 }
 
 cudaError_t launch_amp2(int compute_f32, int ev_f32, const Model& m, const double* coef,

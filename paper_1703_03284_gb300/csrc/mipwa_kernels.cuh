@@ -25,6 +25,8 @@ struct EvalArgs {
   unsigned int* counter;     // finished-block ticket (zero between launches)
   double* out;               // [NLL, dNLL/dparams (P)]
   int* flags;                // bit 0: bad data |A|^2, bit 1: bad norm |A|^2, bit 2: bad I
+  const void* basis_data;    // cached B_r per data event (resonance-major) or null
+  const void* basis_norm;    // the same for the normalisation sample; null: compute B_r
   Model model;
 };
 
@@ -34,6 +36,10 @@ void launch_prepare(const Model& m, const double* params, const double* lu, doub
                     float* coef32, cudaStream_t stream);
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t stream);
+// Cached Breit-Wigner basis of n events: out[r * n + i] = B_r (FP64 form) or
+// B_r / cscale_r (FP32 form), as complex double / float pairs.
+cudaError_t launch_basis(int compute_f32, int ev_f32, const Model& m, const void* ev, int64_t n,
+                         void* out, int grid, cudaStream_t stream);
 cudaError_t launch_amp2(int compute_f32, int ev_f32, const Model& m, const double* coef,
                         const float* coef32, const void* ev, int64_t n, double* out, int grid,
                         cudaStream_t stream);

@@ -230,6 +230,8 @@ extern "C" int mipwa_nll_grad_noalloc(int device, int compute_mode, double mD, d
   a.counter = counter;
   a.out = d_out;
   a.flags = flags;
+  a.basis_data = nullptr;
+  a.basis_norm = nullptr;
   a.model = m;
   CKN(launch_eval(f32, ev32, true, a, nb_d + nb_n, st));
   int h_flags = 0;
