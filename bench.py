@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cached-steps", type=int, default=10)
+    ap.add_argument("--toys-steps", type=int, default=3)
+    ap.add_argument("--n-toys", type=int, default=256)
+    ap.add_argument("--toys-norm", type=int, default=10_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -230,6 +233,79 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
+# ------------------------------------------------------------ batched toys
+def toys_leg(args, stream, rank):
+    """256 toys of the 30-knot pi pi pi model, sizes Poisson around log-uniform
+    means in [1e4, 1e6], a shared 1e7-event normalisation sample; one batched
+    NLL+gradient evaluation (CUDA graph) per step, FP32-mixed with the cached
+    basis, against a loop of single-toy FP64 evaluations."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1703_03284_gb300 import F32, F64, Likelihood
+
+    spec = synth.pipipi(30)
+    truth = synth.true_params(spec)
+    sizes = synth.toy_sizes(args.n_toys, seed=7 + rank)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    gen = Likelihood(torch.cuda.current_device(), F32)
+    gen.set_spec(spec)
+    pool = synth.accept_reject(spec, int(offsets[-1]), lambda x: gen.amp2(truth, x),
+                               seed=11 + 1000 * rank, device="cuda", dtype=torch.float32,
+                               chunk=1 << 24)
+    norm = synth.uniform_in_plot(spec, args.toys_norm, lambda x: gen.inside(x).to(torch.float64),
+                                 seed=12 + 1000 * rank, device="cuda", dtype=torch.float32,
+                                 chunk=1 << 24)
+    params = np.stack([synth.perturbed_params(spec, 500 + t, 0.02) for t in range(args.n_toys)])
+    lik = Likelihood(torch.cuda.current_device(), F32)
+    lik.set_spec(spec)
+    lik.set_norm_sample(norm)
+    lik.set_toys(pool, offsets)
+    lik.enable_basis_cache(True)
+    best = lik.toys_autotune(params)
+    lik.nll_grad_toys(params)
+    launches0 = lik.launch_count()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.toys_steps):
+        lik.nll_grad_toys(params)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1) / args.toys_steps
+    pairs = int(offsets[-1]) + args.n_toys * args.toys_norm
+    # looping single-toy evaluations (a few toys timed, scaled to all toys by events)
+    loop = {}
+    for mode, name in ((F64, "fp64"), (F32, "fp32")):
+        single = Likelihood(torch.cuda.current_device(), mode)
+        single.set_spec(spec)
+        single.set_norm_sample(norm)
+        ev_done, t_done = 0, 0.0
+        for t in range(4):
+            single.set_events(pool[offsets[t]:offsets[t + 1]])
+            single.nll_grad(params[t])
+            torch.cuda.synchronize()
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            single.nll_grad(params[t])
+            l1.record(stream)
+            torch.cuda.synchronize()
+            t_done += l0.elapsed_time(l1)
+            ev_done += int(sizes[t]) + args.toys_norm
+        loop[name] = {"toys_per_s": 1e3 * 4 / t_done, "event_pairs_per_s": ev_done / (t_done / 1e3),
+                      "note": "4 toys timed one by one, same events"}
+    return {"n_toys": args.n_toys, "events_in_toys": int(offsets[-1]),
+            "norm_events": args.toys_norm, "ms_per_iteration": t_ms,
+            "toys_per_s": 1e3 * args.n_toys / t_ms,
+            "event_pairs_per_s": pairs / (t_ms / 1e3),
+            "autotuned_norm_chunk": best,
+            "gpu_launches_per_iteration": (lik.launch_count() - launches0) / args.toys_steps,
+            "loop_single_toy": loop,
+            "speedup_vs_fp64_loop": (1e3 * args.n_toys / t_ms) / loop["fp64"]["toys_per_s"],
+            "dtype": "f32 (cached basis, CUDA graph)"}
+
+
 # ------------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -382,6 +458,12 @@ def run(args, world, rank, local, stream):
                "h2d_bytes_per_step": int(data_h.numel() * 4 + norm_h.numel() * 4 + 8 * P),
                "d2h_bytes_per_step": int(8 * (1 + P) + 4 + 2 * 8)}
 
+    toys = None
+    if args.toys_steps > 0:
+        del lik
+        torch.cuda.empty_cache()
+        toys = toys_leg(args, stream, rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec, params)
@@ -395,8 +477,8 @@ def run(args, world, rank, local, stream):
             "config": {"workload": WORKLOAD, "n_data": n, "n_norm": n,
                        "l2": "inputs (1.6 GB) larger than L2 (129 MB); no flush needed",
                        "parallelism": f"replicas x{world} (no collective)"},
-            "roofline": roofline, "fp64_plain": fp64, "fp32_cached_basis": cached, "e2e": e2e,
-            "cpu_baseline": cpu,
+            "roofline": roofline, "fp64_plain": fp64, "fp32_cached_basis": cached,
+            "batched_toys": toys, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)
 

@@ -83,6 +83,7 @@ enum {
 /* Limits of one context. */
 #define MIPWA_MAX_RES 4
 #define MIPWA_MAX_KNOTS 64
+#define MIPWA_MAX_TOYS 4096
 
 /* Create a context on CUDA device `device` computing in `compute_mode`
  * (MIPWA_F64 or MIPWA_F32). The context owns a non-blocking CUDA stream until
@@ -148,6 +149,32 @@ int mipwa_nll(mipwa_ctx* ctx, const double* params, double* nll);
  * adjoint of the per-event amplitude (amplitudes recomputed, nothing stored
  * per event). Blocks until done. */
 int mipwa_nll_grad(mipwa_ctx* ctx, const double* params, double* nll, double* grad);
+
+/* Batched toys (the fit-quality test of Sec. 4: many toy samples generated
+ * from the PDF and fitted). n_toys (1..MIPWA_MAX_TOYS) data samples stored
+ * back to back: toy t owns events [offsets[t], offsets[t+1]) of the n_total
+ * pairs at s12s13 (offsets: n_toys + 1 host int64, offsets[0] = 0,
+ * offsets[n_toys] = n_total, non-decreasing; empty toys allowed). All toys
+ * share the normalisation sample of mipwa_set_norm_sample. Same storage,
+ * validation and ownership rules as mipwa_set_events. */
+int mipwa_set_toys(mipwa_ctx* ctx, const void* s12s13, int64_t n_total, int dtype,
+                   int on_device, const int64_t* offsets, int n_toys, int64_t* n_outside);
+
+/* NLL and gradient of every toy at its own parameter vector, in one launch of
+ * a captured CUDA graph (parameter copy, spline setup for all toys, one
+ * persistent kernel over a work list of (toy, event range) items, per-toy
+ * reduction, result copy). params: n_toys * P host doubles (toy-major);
+ * nll: n_toys; grad: n_toys * P. Blocks until done. */
+int mipwa_nll_grad_toys(mipwa_ctx* ctx, const double* params, double* nll, double* grad);
+
+/* Time the batched evaluation at `params` for normalisation chunk sizes of
+ * 65536 ... 2097152 events per work item and keep the fastest (written to
+ * *best_chunk if not NULL). */
+int mipwa_toys_autotune(mipwa_ctx* ctx, const double* params, int64_t* best_chunk);
+
+/* Capture the batched evaluation in a CUDA graph (on != 0, the default) or
+ * launch its kernels one by one. */
+int mipwa_set_toys_graph(mipwa_ctx* ctx, int on);
 
 /* |A(s12,s13)|^2 at `params` for n events at the DEVICE pointer `d_s12s13`
  * (type dtype), written as doubles to the DEVICE pointer `d_out`; events

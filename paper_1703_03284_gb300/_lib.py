@@ -15,6 +15,7 @@ OK, EINVAL, EOUTSIDE, ENONPOS, ECUDA, ETIMEOUT, ESTATE, ENOMEM = 0, -1, -2, -3, 
 F64, F32 = 0, 1
 MAX_RES = 4
 MAX_KNOTS = 64
+MAX_TOYS = 4096
 
 STATUS_NAMES = {OK: "MIPWA_OK", EINVAL: "MIPWA_EINVAL", EOUTSIDE: "MIPWA_EOUTSIDE",
                 ENONPOS: "MIPWA_ENONPOS", ECUDA: "MIPWA_ECUDA", ETIMEOUT: "MIPWA_ETIMEOUT",
@@ -42,6 +43,10 @@ SIGNATURES = [
     ("mipwa_num_params", _i, [_vp]),
     ("mipwa_nll", _i, [_vp, _pd, _pd]),
     ("mipwa_nll_grad", _i, [_vp, _pd, _pd, _pd]),
+    ("mipwa_set_toys", _i, [_vp, _vp, _i64, _i, _i, _pi64, _i, _pi64]),
+    ("mipwa_nll_grad_toys", _i, [_vp, _pd, _pd, _pd]),
+    ("mipwa_toys_autotune", _i, [_vp, _pd, _pi64]),
+    ("mipwa_set_toys_graph", _i, [_vp, _i]),
     ("mipwa_amp2", _i, [_vp, _pd, _vp, _i64, _i, _vp]),
     ("mipwa_inside", _i, [_vp, _vp, _i64, _i, _vp]),
     ("mipwa_nll_grad_noalloc", _i, [_i, _i, _d, _d, _d, ctypes.POINTER(Resonance), _i, _pd, _i,

@@ -136,6 +136,43 @@ class Likelihood:
     def enable_basis_cache(self, on: bool = True):
         self._check(self._lib.mipwa_enable_basis_cache(self._h, int(bool(on))))
 
+    def set_toys(self, events, offsets):
+        """Toy data samples back to back; toy t owns events[offsets[t]:offsets[t+1]]."""
+        self._follow_stream()
+        ptr, n, code, on_dev, keep = _event_buffer(events)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        n_out = ctypes.c_int64(0)
+        rc = self._lib.mipwa_set_toys(self._h, ctypes.c_void_p(ptr), n, code, on_dev,
+                                      off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      len(off) - 1, ctypes.byref(n_out))
+        del keep
+        self._check(rc, n_out.value)
+        self.n_toys = len(off) - 1
+
+    def nll_grad_toys(self, params):
+        """params: (n_toys, P) -> (nll (n_toys,), grad (n_toys, P))."""
+        self._follow_stream()
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        if p.shape != (self.n_toys, self.n_params):
+            raise ValueError(f"expected params of shape {(self.n_toys, self.n_params)}")
+        nll = np.empty(self.n_toys)
+        g = np.empty_like(p)
+        pd = ctypes.POINTER(ctypes.c_double)
+        self._check(self._lib.mipwa_nll_grad_toys(self._h, p.ctypes.data_as(pd),
+                                                  nll.ctypes.data_as(pd), g.ctypes.data_as(pd)))
+        return nll, g
+
+    def toys_autotune(self, params) -> int:
+        self._follow_stream()
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        best = ctypes.c_int64(0)
+        self._check(self._lib.mipwa_toys_autotune(
+            self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(best)))
+        return best.value
+
+    def set_toys_graph(self, on: bool = True):
+        self._check(self._lib.mipwa_set_toys_graph(self._h, int(bool(on))))
+
     def num_params(self) -> int:
         return int(self._lib.mipwa_num_params(self._h))
 

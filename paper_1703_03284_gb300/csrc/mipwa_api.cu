@@ -52,8 +52,40 @@ struct mipwa_ctx {
     void* basis = nullptr;  // cached B_r per event (resonance-major)
     size_t basis_cap = 0;
     bool basis_valid = false;
-  } data, norm;
+    bool no_sort = false;   // keep the caller's order (toy ranges)
+  } data, norm, toys;
   bool basis_on = false;
+  // batched toys
+  struct Toys {
+    int n = 0;
+    std::vector<int64_t> offsets;
+    int64_t* d_offsets = nullptr;
+    size_t d_offsets_cap = 0;
+    ToyItem* d_items = nullptr;
+    size_t d_items_cap = 0;
+    int* d_data_rows = nullptr;
+    size_t d_data_rows_cap = 0;
+    unsigned int* d_queue = nullptr;
+    double* d_params = nullptr;
+    size_t d_params_cap = 0;
+    double* d_coef = nullptr;
+    size_t d_coef_cap = 0;
+    float* d_coef32 = nullptr;
+    size_t d_coef32_cap = 0;
+    double* d_out = nullptr;
+    size_t d_out_cap = 0;
+    double* d_partials = nullptr;
+    size_t d_partials_cap = 0;
+    double* h_params = nullptr;  // pinned
+    double* h_out = nullptr;     // pinned (1+P per toy, then the flags)
+    size_t h_cap = 0;            // doubles of each pinned buffer
+    int n_items = 0, rows_per_toy = 0, norm_chunks = 0, grid = 0;
+    int64_t norm_chunk = 131072, data_chunk = 65536;
+    bool planned = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool use_graph = true;
+  } tq;
   int64_t launches = 0;
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -226,7 +258,17 @@ int sort_into(mipwa_ctx* c, const void* src, int64_t n, int dtype, void* dst) {
 
 bool sortable(int64_t n) { return n > 1 && n < (int64_t)0x7fffffff; }
 
-void invalidate_basis(mipwa_ctx* c) { c->data.basis_valid = c->norm.basis_valid = false; }
+void invalidate_graph(mipwa_ctx* c) {
+  if (c->tq.exec) cudaGraphExecDestroy(c->tq.exec);
+  if (c->tq.graph) cudaGraphDestroy(c->tq.graph);
+  c->tq.exec = nullptr;
+  c->tq.graph = nullptr;
+}
+
+void invalidate_basis(mipwa_ctx* c) {
+  c->data.basis_valid = c->norm.basis_valid = c->toys.basis_valid = false;
+  invalidate_graph(c);
+}
 
 // (Re)build the cached Breit-Wigner basis of a sample for the current model
 // and compute mode.
@@ -279,7 +321,7 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
                 (long long)n);
   }
   smp.sorted = false;
-  if (c->have_model && sortable(n)) {
+  if (c->have_model && sortable(n) && !smp.no_sort) {
     // the old sample is no longer needed: sort the validated copy into it
     rc = ensure(c, &smp.cur, &smp.cur_cap, bytes);
     if (rc) return rc;
@@ -295,12 +337,13 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
   smp.dtype = dtype;
   smp.set = true;
   smp.basis_valid = false;
+  invalidate_graph(c);
   return MIPWA_OK;
 }
 
 // Re-group a stored sample for the current knots (after set_model).
 int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
-  if (!smp.set || !sortable(smp.n)) return MIPWA_OK;
+  if (!smp.set || !sortable(smp.n) || smp.no_sort) return MIPWA_OK;
   const size_t bytes = (size_t)smp.n * ev_bytes(smp.dtype);
   int rc = ensure(c, &smp.spare, &smp.spare_cap, bytes);
   if (rc) return rc;
@@ -405,6 +448,142 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   return MIPWA_OK;
 }
 
+// ----------------------------------------------------------- batched toys
+// Work list of the batched launch: normalisation items chunk-major (every toy
+// of chunk 0, then of chunk 1, ...), then each toy's data ranges.
+int plan_toys(mipwa_ctx* c) {
+  auto& q = c->tq;
+  const int T = q.n;
+  const int64_t nn = c->norm.n;
+  const int C = (int)((nn + q.norm_chunk - 1) / q.norm_chunk);
+  std::vector<int> drows(T);
+  int dmax = 0;
+  for (int t = 0; t < T; ++t) {
+    const int64_t nt = q.offsets[t + 1] - q.offsets[t];
+    drows[t] = (int)((nt + q.data_chunk - 1) / q.data_chunk);
+    dmax = std::max(dmax, drows[t]);
+  }
+  const int rpt = C + dmax;
+  std::vector<ToyItem> items;
+  items.reserve((size_t)T * C + (size_t)T * dmax);
+  for (int ch = 0; ch < C; ++ch)
+    for (int t = 0; t < T; ++t)
+      items.push_back(ToyItem{t, 0, (int64_t)ch * q.norm_chunk,
+                              std::min(nn, (int64_t)(ch + 1) * q.norm_chunk), t * rpt + ch});
+  for (int t = 0; t < T; ++t)
+    for (int d = 0; d < drows[t]; ++d) {
+      const int64_t b = q.offsets[t] + (int64_t)d * q.data_chunk;
+      items.push_back(ToyItem{t, 1, b, std::min(q.offsets[t + 1], b + q.data_chunk),
+                              t * rpt + C + d});
+    }
+  const int W = partial_width(c->model.kn.n, c->model.n_res, true);
+  int rc = ensure(c, (void**)&q.d_items, &q.d_items_cap, items.size() * sizeof(ToyItem));
+  if (!rc) rc = ensure(c, (void**)&q.d_data_rows, &q.d_data_rows_cap, T * sizeof(int));
+  if (!rc) rc = ensure(c, (void**)&q.d_partials, &q.d_partials_cap,
+                       (size_t)T * rpt * W * sizeof(double));
+  if (rc) return rc;
+  CK(c, cudaMemcpyAsync(q.d_items, items.data(), items.size() * sizeof(ToyItem),
+                        cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(q.d_data_rows, drows.data(), T * sizeof(int), cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  q.n_items = (int)items.size();
+  q.rows_per_toy = rpt;
+  q.norm_chunks = C;
+  q.planned = true;
+  invalidate_graph(c);
+  return MIPWA_OK;
+}
+
+// Queue one batched evaluation (params already in q.h_params) on `st`.
+int enqueue_toys(mipwa_ctx* c, cudaStream_t st) {
+  auto& q = c->tq;
+  const int T = q.n, P = c->n_params;
+  const int f32 = c->mode == MIPWA_F32;
+  const int ev32 = c->norm.dtype == MIPWA_F32;
+  CK(c, cudaMemcpyAsync(q.d_params, q.h_params, (size_t)T * P * sizeof(double),
+                        cudaMemcpyHostToDevice, st));
+  CK(c, cudaMemsetAsync(q.d_queue, 0, sizeof(unsigned int), st));
+  CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), st));
+  launch_prepare(c->model, q.d_params, c->d_lu, q.d_coef, q.d_coef32, st, T);
+  CK(c, cudaGetLastError());
+  ToyArgs a;
+  a.data = c->toys.cur;
+  a.norm = c->norm.cur;
+  a.n_data = c->toys.n;
+  a.n_norm = c->norm.n;
+  a.offsets = q.d_offsets;
+  a.n_toys = T;
+  a.items = q.d_items;
+  a.n_items = q.n_items;
+  a.queue = q.d_queue;
+  a.rows_per_toy = q.rows_per_toy;
+  a.norm_chunks = q.norm_chunks;
+  a.data_rows = q.d_data_rows;
+  a.coef = q.d_coef;
+  a.coef32 = q.d_coef32;
+  a.lu = c->d_lu;
+  a.partials = q.d_partials;
+  a.out = q.d_out;
+  a.flags = c->d_flags;
+  a.basis_data = c->basis_on ? c->toys.basis : nullptr;
+  a.basis_norm = c->basis_on ? c->norm.basis : nullptr;
+  a.model = c->model;
+  CK(c, launch_toys(f32, ev32, a, q.grid, st));
+  CK(c, cudaMemcpyAsync(q.h_out, q.d_out, (size_t)T * (1 + P) * sizeof(double),
+                        cudaMemcpyDeviceToHost, st));
+  CK(c, cudaMemcpyAsync(q.h_out + (size_t)T * (1 + P), c->d_flags, sizeof(int),
+                        cudaMemcpyDeviceToHost, st));
+  return MIPWA_OK;
+}
+
+// Everything a batched evaluation needs, then one launch of the captured graph
+// (or the plain launch sequence when graphs are off).
+int run_toys(mipwa_ctx* c) {
+  auto& q = c->tq;
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  if (!c->norm.set) return fail(c, MIPWA_ESTATE, "set_norm_sample must come first");
+  if (!c->toys.set || q.n == 0) return fail(c, MIPWA_ESTATE, "set_toys must come first");
+  if (c->toys.n > 0 && c->toys.dtype != c->norm.dtype)
+    return fail(c, MIPWA_EINVAL, "toy and normalisation samples must share a dtype");
+  int rc;
+  if (c->basis_on) {
+    rc = build_basis(c, c->toys);
+    if (!rc) rc = build_basis(c, c->norm);
+    if (rc) return rc;
+  }
+  if (!q.planned) {
+    rc = plan_toys(c);
+    if (rc) return rc;
+  }
+  // persistent grid: every SM full (computed outside any stream capture)
+  q.grid = c->sm_count * toys_blocks_per_sm(c->mode == MIPWA_F32, c->norm.dtype == MIPWA_F32);
+  if (q.use_graph) {
+    if (!q.exec) {
+      CK(c, cudaStreamSynchronize(c->stream));
+      CK(c, cudaStreamBeginCapture(c->own_stream, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_toys(c, c->own_stream);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->own_stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return fail(c, MIPWA_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+      q.graph = g;
+      CK(c, cudaGraphInstantiate(&q.exec, q.graph, 0));
+    }
+    CK(c, cudaGraphLaunch(q.exec, c->stream));
+    c->launches += 3;
+  } else {
+    rc = enqueue_toys(c, c->stream);
+    if (rc) return rc;
+    c->launches += 3;
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return MIPWA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -461,6 +640,14 @@ void mipwa_destroy(mipwa_ctx* c) {
                   c->norm.spare})
     if (p) cudaFree(p);
   if (c->h_stage) cudaFreeHost(c->h_stage);
+  invalidate_graph(c);
+  for (void* p : {(void*)c->tq.d_offsets, (void*)c->tq.d_items, (void*)c->tq.d_data_rows,
+                  (void*)c->tq.d_queue, (void*)c->tq.d_params, (void*)c->tq.d_coef,
+                  (void*)c->tq.d_coef32, (void*)c->tq.d_out, (void*)c->tq.d_partials,
+                  c->toys.cur, c->toys.spare, c->toys.basis})
+    if (p) cudaFree(p);
+  if (c->tq.h_params) cudaFreeHost(c->tq.h_params);
+  if (c->tq.h_out) cudaFreeHost(c->tq.h_out);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -549,6 +736,7 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   c->model = m;
   c->n_params = 2 * n_res + 2 * n_knots;
   c->have_model = true;
+  c->tq.planned = false;
   invalidate_basis(c);
   rc = resort(c, c->data);
   if (rc) return rc;
@@ -564,7 +752,12 @@ int mipwa_set_events(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, int on
 int mipwa_set_norm_sample(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, int on_device,
                           int64_t* n_outside) {
   if (!c) return MIPWA_EINVAL;
-  return set_sample(c, c->norm, ptr, n, dtype, on_device, n_outside, false);
+  const int rc = set_sample(c, c->norm, ptr, n, dtype, on_device, n_outside, false);
+  if (rc == MIPWA_OK) {
+    c->tq.planned = false;
+    invalidate_graph(c);
+  }
+  return rc;
 }
 
 int mipwa_num_params(const mipwa_ctx* c) { return (c && c->have_model) ? c->n_params : -1; }
@@ -575,6 +768,119 @@ int mipwa_nll(mipwa_ctx* c, const double* params, double* nll) {
 
 int mipwa_nll_grad(mipwa_ctx* c, const double* params, double* nll, double* grad) {
   return evaluate(c, params, nll, grad, true);
+}
+
+int mipwa_set_toys(mipwa_ctx* c, const void* ptr, int64_t n_total, int dtype, int on_device,
+                   const int64_t* offsets, int n_toys, int64_t* n_outside) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (n_toys < 1 || n_toys > MIPWA_MAX_TOYS || !offsets)
+    return fail(c, MIPWA_EINVAL, "n_toys must be in 1..%d", MIPWA_MAX_TOYS);
+  if (offsets[0] != 0 || offsets[n_toys] != n_total)
+    return fail(c, MIPWA_EINVAL, "offsets must run from 0 to n_total");
+  for (int t = 0; t < n_toys; ++t)
+    if (offsets[t + 1] < offsets[t]) return fail(c, MIPWA_EINVAL, "offsets must not decrease");
+  c->toys.no_sort = true;
+  rc = set_sample(c, c->toys, ptr, n_total, dtype, on_device, n_outside, true);
+  if (rc) return rc;
+  auto& q = c->tq;
+  rc = ensure(c, (void**)&q.d_offsets, &q.d_offsets_cap, (n_toys + 1) * sizeof(int64_t));
+  if (rc) return rc;
+  CK(c, cudaMemcpyAsync(q.d_offsets, offsets, (n_toys + 1) * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, c->stream));
+  const int P = 2 * kMaxRes + 2 * kMaxKnots;  // room for any model
+  rc = ensure(c, (void**)&q.d_params, &q.d_params_cap, (size_t)n_toys * P * sizeof(double));
+  if (!rc) rc = ensure(c, (void**)&q.d_coef, &q.d_coef_cap,
+                       (size_t)n_toys * coef_size(kMaxKnots, kMaxRes) * sizeof(double));
+  if (!rc) rc = ensure(c, (void**)&q.d_coef32, &q.d_coef32_cap,
+                       (size_t)n_toys * coef32_size(kMaxKnots, kMaxRes) * sizeof(float));
+  if (!rc) rc = ensure(c, (void**)&q.d_out, &q.d_out_cap, (size_t)n_toys * (1 + P) * sizeof(double));
+  if (rc) return rc;
+  if (!q.d_queue) CK(c, cudaMalloc(&q.d_queue, sizeof(unsigned int)));
+  const size_t hneed = (size_t)n_toys * (1 + P) + 1;
+  if (q.h_cap < hneed) {
+    if (q.h_params) cudaFreeHost(q.h_params);
+    if (q.h_out) cudaFreeHost(q.h_out);
+    q.h_params = q.h_out = nullptr;
+    q.h_cap = 0;
+    CK(c, cudaMallocHost(&q.h_params, hneed * sizeof(double)));
+    CK(c, cudaMallocHost(&q.h_out, hneed * sizeof(double)));
+    q.h_cap = hneed;
+  }
+  q.offsets.assign(offsets, offsets + n_toys + 1);
+  q.n = n_toys;
+  q.planned = false;
+  invalidate_graph(c);
+  CK(c, cudaStreamSynchronize(c->stream));
+  return MIPWA_OK;
+}
+
+int mipwa_nll_grad_toys(mipwa_ctx* c, const double* params, double* nll, double* grad) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!params || !nll || !grad) return fail(c, MIPWA_EINVAL, "null pointer");
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  auto& q = c->tq;
+  const int T = q.n, P = c->n_params;
+  if (T == 0) return fail(c, MIPWA_ESTATE, "set_toys must come first");
+  for (size_t k = 0; k < (size_t)T * P; ++k)
+    if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %zu is not finite", k);
+  std::memcpy(q.h_params, params, (size_t)T * P * sizeof(double));
+  rc = run_toys(c);
+  if (rc) return rc;
+  const int flags = *(const int*)(q.h_out + (size_t)T * (1 + P));
+  if (flags & kFlagData) return fail(c, MIPWA_ENONPOS, "|A|^2 <= 0 or non-finite for a toy event");
+  if (flags & (kFlagNorm | kFlagIntegral))
+    return fail(c, MIPWA_ENONPOS, "normalisation integral is not positive and finite");
+  for (int t = 0; t < T; ++t) {
+    const double* o = q.h_out + (size_t)t * (1 + P);
+    nll[t] = o[0];
+    std::memcpy(grad + (size_t)t * P, o + 1, P * sizeof(double));
+  }
+  return MIPWA_OK;
+}
+
+int mipwa_toys_autotune(mipwa_ctx* c, const double* params, int64_t* best_chunk) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!params) return fail(c, MIPWA_EINVAL, "null pointer");
+  auto& q = c->tq;
+  const int T = q.n, P = c->n_params;
+  if (T == 0 || !c->have_model) return fail(c, MIPWA_ESTATE, "set_toys and set_model first");
+  std::memcpy(q.h_params, params, (size_t)T * P * sizeof(double));
+  const int64_t cand[] = {65536, 131072, 262144, 524288, 1048576, 2097152};
+  float best_ms = 0.0f;
+  int64_t best = q.norm_chunk;
+  cudaEvent_t e0 = c->ev0, e1 = c->ev1;
+  for (int64_t ch : cand) {
+    q.norm_chunk = ch;
+    q.planned = false;
+    rc = run_toys(c);  // plan, capture and warm up
+    if (rc) return rc;
+    CK(c, cudaEventRecord(e0, c->stream));
+    rc = run_toys(c);
+    if (rc) return rc;
+    CK(c, cudaEventRecord(e1, c->stream));
+    CK(c, cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CK(c, cudaEventElapsedTime(&ms, e0, e1));
+    if (best_ms == 0.0f || ms < best_ms) {
+      best_ms = ms;
+      best = ch;
+    }
+  }
+  q.norm_chunk = best;
+  q.planned = false;
+  if (best_chunk) *best_chunk = best;
+  return MIPWA_OK;
+}
+
+int mipwa_set_toys_graph(mipwa_ctx* c, int on) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->tq.use_graph = on != 0;
+  invalidate_graph(c);
+  return MIPWA_OK;
 }
 
 int mipwa_amp2(mipwa_ctx* c, const double* params, const void* ev, int64_t n, int dtype,

@@ -339,27 +339,28 @@ __device__ __forceinline__ void bin_swave_warp(EvalSmem<T>& sm, bool valid, int 
   }
 }
 
-// The last block: reduce block rows in order, then -2 ln L, its gradient, and
-// the adjoint of the natural-spline solve (ybar += D^T T^{-1} Mbar).
+// Reduce partial rows in a fixed order, then -2 ln L, its gradient and the
+// adjoint of the natural-spline solve (ybar += D^T T^{-1} Mbar). Data rows are
+// [d0, d0 + dn), normalisation rows [n0, n0 + nn); writes out[0..P].
 template <typename T, bool GRAD>
-__device__ void finalize(EvalSmem<T>& sm, const EvalArgs& a) {
-  const Model& m = a.model;
+__device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
+                              const double* partials, int d0, int dn, int n0, int nn,
+                              int64_t n_data, int64_t n_norm, double* out, int* flags) {
   const int R = m.n_res, N = m.kn.n, nseg = N - 1;
   const int W = partial_width(N, R, GRAD);
   for (int col = threadIdx.x; col < W; col += blockDim.x) {
     double sd = 0.0, sn = 0.0;
-    for (int row = 0; row < a.nb_data; ++row) sd += __ldcg(&a.partials[(size_t)row * W + col]);
-    for (int row = a.nb_data; row < a.nb_data + a.nb_norm; ++row)
-      sn += __ldcg(&a.partials[(size_t)row * W + col]);
+    for (int row = d0; row < d0 + dn; ++row) sd += __ldcg(&partials[(size_t)row * W + col]);
+    for (int row = n0; row < n0 + nn; ++row) sn += __ldcg(&partials[(size_t)row * W + col]);
     sm.fin_d[col] = sd;
     sm.fin_n[col] = sn;
   }
   __syncthreads();
   const double S = sm.fin_n[0];
-  const double nd = (double)a.n_data;
+  const double nd = (double)n_data;
   if (threadIdx.x == 0) {
-    if (!(S > 0.0) || !isfinite(S)) atomicOr(a.flags, kFlagIntegral);
-    a.out[0] = -2.0 * sm.fin_d[0] + 2.0 * nd * log(S / (double)a.n_norm);
+    if (!(S > 0.0) || !isfinite(S)) atomicOr(flags, kFlagIntegral);
+    out[0] = -2.0 * sm.fin_d[0] + 2.0 * nd * log(S / (double)n_norm);
   }
   if constexpr (GRAD) {
     const double kappa = 2.0 * nd / S;
@@ -369,14 +370,14 @@ __device__ void finalize(EvalSmem<T>& sm, const EvalArgs& a) {
     for (int k = threadIdx.x; k < 2 * R; k += blockDim.x) {
       // FP32 form: the kernel accumulated against A_r / cscale_r
       const double sc = std::is_same<T, float>::value ? m.cscale[k >> 1] : 1.0;
-      a.out[1 + k] = sm.fin_d[1 + k] * sc;
+      out[1 + k] = sm.fin_d[1 + k] * sc;
     }
     // one thread per spline, in different warps
     const int sp = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 ? 1 : -1);
     if (sp >= 0) {
-      const double* h = a.lu;
-      const double* ih = a.lu + nseg;
-      const double* w = a.lu + 2 * nseg;
+      const double* h = lu;
+      const double* ih = lu + nseg;
+      const double* w = lu + 2 * nseg;
       const double* idia = w + (N - 2);
       const double* sup = idia + (N - 2);
       double* yb = sm.ybar[sp];
@@ -406,18 +407,21 @@ __device__ void finalize(EvalSmem<T>& sm, const EvalArgs& a) {
           yb[k - 1] += vk * ih[k - 1];
         }
       }
-      for (int k = 0; k < N; ++k) a.out[1 + 2 * R + sp * N + k] = yb[k];
+      for (int k = 0; k < N; ++k) out[1 + 2 * R + sp * N + k] = yb[k];
     }
   }
-  if (threadIdx.x == 0) *a.counter = 0u;
 }
 
+// Accumulate the events first, first + stride, ... < end of one sample
+// (cached basis: resonance-major over the sample's n events) into one partial
+// row: [sum ln|A|^2 (data) or sum |A|^2 (normalisation), c_r adjoint (2R),
+// spline polynomial adjoints (8 (N-1))]. The per-evaluation model data must be
+// staged in sm; the bins are zeroed here. Every thread of the block calls this.
 template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED>
-__global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
-  __shared__ EvalSmem<T> sm;
-  const Model& m = a.model;
+__device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
+                                 const Cplx<T>* cached, int64_t n, int64_t first, int64_t end,
+                                 int64_t stride, bool is_data, double* row, int* flags) {
   const int R = m.n_res, nseg = m.kn.n - 1;
-  stage(sm, m, EvalCoefs{a.coef, a.coef32});
   if constexpr (GRAD) {
     for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) {
       sm.bind[i] = 0.0;
@@ -425,16 +429,6 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
     }
   }
   __syncthreads();
-
-  const bool is_data = (int)blockIdx.x < a.nb_data;
-  const int64_t n = is_data ? a.n_data : a.n_norm;
-  const int nb = is_data ? a.nb_data : a.nb_norm;
-  const int b = is_data ? (int)blockIdx.x : (int)blockIdx.x - a.nb_data;
-  const EvT* ev = reinterpret_cast<const EvT*>(is_data ? a.data : a.norm);
-  const Cplx<T>* cached =
-      reinterpret_cast<const Cplx<T>*>(is_data ? a.basis_data : a.basis_norm);
-  const int64_t stride = (int64_t)nb * kThreads;
-
   Acc<T> sum;
   T gc[2 * kMaxRes];  // c_r adjoint: plain sums (gradient tolerance), FP64 per block
 #pragma unroll
@@ -442,14 +436,14 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
   long long sum_e = 0;  // FP32 form, data: sum of binary exponents of |A|^2
   int bad = 0;
   int iter = 0;
-  for (int64_t base = (int64_t)b * kThreads; base < n; base += stride) {
+  for (int64_t base = first; base < end; base += stride) {
     const int64_t i = base + threadIdx.x;
     bool ok = false;
     SwavePart<T> w12, w13;
     Cplx<T> A{T(0), T(0)};
     Cplx<T> B[kMaxRes];
     T wt = T(1);
-    if (i < n) {
+    if (i < end) {
       const EvT e = ev[i];
       const T s12 = (T)e.x, s13 = (T)e.y;
       A = amplitude<T, SIG, CACHED>(m, sm, s12, s13, cached, i, n, B, w12, w13);
@@ -461,10 +455,11 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
             int ex;
             sum.add(log_split(A2, ex));
             sum_e += ex;
+            wt = rcp_nr(A2);
           } else {
             sum.add(log(A2));
+            wt = T(1) / A2;
           }
-          if constexpr (std::is_same<T, float>::value) wt = rcp_nr(A2); else wt = T(1) / A2;
         }
       } else {
         ok = isfinite(A2);
@@ -503,7 +498,7 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
       }
     }
   }
-  if (bad) atomicOr(a.flags, is_data ? kFlagData : kFlagNorm);
+  if (bad) atomicOr(flags, is_data ? kFlagData : kFlagNorm);
   if constexpr (GRAD && std::is_same<T, float>::value) {
     __syncthreads();
     for (int k = threadIdx.x; k < nseg * 8; k += blockDim.x) sm.bind[k] += (double)sm.binf[k];
@@ -522,8 +517,6 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
     }
   }
   __syncthreads();
-  const int W = partial_width(m.kn.n, R, GRAD);
-  double* row = a.partials + (size_t)blockIdx.x * W;
   if (threadIdx.x < nred) {
     double v = 0.0;
     for (int wv = 0; wv < kThreads / 32; ++wv) v += sm.red[wv][threadIdx.x];
@@ -532,6 +525,24 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
   if constexpr (GRAD) {
     for (int k = threadIdx.x; k < nseg * 8; k += blockDim.x) row[1 + 2 * R + k] = sm.bind[k];
   }
+}
+
+template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED>
+__global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
+  __shared__ EvalSmem<T> sm;
+  const Model& m = a.model;
+  stage(sm, m, EvalCoefs{a.coef, a.coef32});
+  const bool is_data = (int)blockIdx.x < a.nb_data;
+  const int64_t n = is_data ? a.n_data : a.n_norm;
+  const int nb = is_data ? a.nb_data : a.nb_norm;
+  const int b = is_data ? (int)blockIdx.x : (int)blockIdx.x - a.nb_data;
+  const EvT* ev = reinterpret_cast<const EvT*>(is_data ? a.data : a.norm);
+  const Cplx<T>* cached =
+      reinterpret_cast<const Cplx<T>*>(is_data ? a.basis_data : a.basis_norm);
+  const int W = partial_width(m.kn.n, m.n_res, GRAD);
+  accumulate_range<T, EvT, GRAD, SIG, CACHED>(sm, m, ev, cached, n, (int64_t)b * kThreads, n,
+                                              (int64_t)nb * kThreads, is_data,
+                                              a.partials + (size_t)blockIdx.x * W, a.flags);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -541,7 +552,53 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
   __syncthreads();
   if (!sm.is_last) return;
   __threadfence();
-  finalize<T, GRAD>(sm, a);
+  finalize_rows<T, GRAD>(sm, m, a.lu, a.partials, 0, a.nb_data, a.nb_data, a.nb_norm, a.n_data,
+                         a.n_norm, a.out, a.flags);
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// -------------------------------------------------------------- batched toys
+// One persistent launch for all toys: blocks take work items from a queue;
+// an item is a range of one toy's data events or a chunk of the shared
+// normalisation sample for one toy, and writes one partial row. Items come
+// chunk-major (all toys of a normalisation chunk in turn), so a chunk is read
+// from HBM once and then from L2.
+template <typename T, typename EvT, bool CACHED>
+__global__ void __launch_bounds__(kThreads) toys_kernel(const ToyArgs a) {
+  __shared__ EvalSmem<T> sm;
+  __shared__ int item_sh;
+  const Model& m = a.model;
+  const int W = partial_width(m.kn.n, m.n_res, true);
+  const int cs = coef_size(m.kn.n, m.n_res), cs32 = coef32_size(m.kn.n, m.n_res);
+  for (;;) {
+    __syncthreads();  // the previous item is done with sm and item_sh
+    if (threadIdx.x == 0) item_sh = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int item = item_sh;
+    if (item >= a.n_items) break;
+    const ToyItem it = a.items[item];
+    stage(sm, m, EvalCoefs{a.coef + (size_t)it.toy * cs, a.coef32 + (size_t)it.toy * cs32});
+    const EvT* ev = reinterpret_cast<const EvT*>(it.is_data ? a.data : a.norm);
+    const Cplx<T>* cached =
+        reinterpret_cast<const Cplx<T>*>(it.is_data ? a.basis_data : a.basis_norm);
+    const int64_t n = it.is_data ? a.n_data : a.n_norm;
+    accumulate_range<T, EvT, true, 0, CACHED>(sm, m, ev, cached, n, it.start, it.end,
+                                              (int64_t)kThreads, it.is_data != 0,
+                                              a.partials + (size_t)it.row * W, a.flags);
+  }
+}
+
+// One block per toy: reduce the toy's rows, write [NLL_t, grad_t].
+template <typename T>
+__global__ void __launch_bounds__(kThreads) toys_finalize_kernel(const ToyArgs a) {
+  __shared__ SmemCommon sm;
+  const int t = blockIdx.x;
+  const int P = 2 * a.model.n_res + 2 * a.model.kn.n;
+  const int base = t * a.rows_per_toy;
+  const int64_t n_data = a.offsets[t + 1] - a.offsets[t];
+  finalize_rows<T, true>(sm, a.model, a.lu, a.partials, base + a.norm_chunks,
+                         a.data_rows[t], base, a.norm_chunks, n_data, a.n_norm,
+                         a.out + (size_t)t * (1 + P), a.flags);
 }
 
 // ----------------------------------------------------------- |A|^2 per event
@@ -635,6 +692,48 @@ cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& 
   }
   if (ev_f32) return dispatch_eval<double, float2>(grad, cached, pd, a, grid, st);
   return dispatch_eval<double, double2>(grad, cached, pd, a, grid, st);
+}
+
+template <typename T, typename EvT>
+static cudaError_t run_toys(bool cached, const ToyArgs& a, int grid, cudaStream_t st) {
+  if (cached) toys_kernel<T, EvT, true><<<grid, kThreads, 0, st>>>(a);
+  else toys_kernel<T, EvT, false><<<grid, kThreads, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  toys_finalize_kernel<T><<<a.n_toys, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int grid,
+                        cudaStream_t st) {
+  const bool cached = a.basis_norm != nullptr;
+  if (compute_f32) return ev_f32 ? run_toys<float, float2>(cached, a, grid, st)
+                                 : run_toys<float, double2>(cached, a, grid, st);
+  return ev_f32 ? run_toys<double, float2>(cached, a, grid, st)
+                : run_toys<double, double2>(cached, a, grid, st);
+}
+
+int toys_blocks_per_sm(int compute_f32, int ev_f32) {
+  int a = 0, b = 0;
+  if (compute_f32) {
+    if (ev_f32) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, toys_kernel<float, float2, false>, kThreads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, toys_kernel<float, float2, true>, kThreads, 0);
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, toys_kernel<float, double2, false>, kThreads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, toys_kernel<float, double2, true>, kThreads, 0);
+    }
+  } else {
+    if (ev_f32) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, toys_kernel<double, float2, false>, kThreads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, toys_kernel<double, float2, true>, kThreads, 0);
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, toys_kernel<double, double2, false>, kThreads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, toys_kernel<double, double2, true>, kThreads, 0);
+    }
+  }
+  const int v = a < b ? a : b;
+  return v > 0 ? v : 1;
 }
 
 cudaError_t launch_basis(int compute_f32, int ev_f32, const Model& m, const void* ev, int64_t n,

@@ -32,8 +32,44 @@ struct EvalArgs {
 
 enum { kFlagData = 1, kFlagNorm = 2, kFlagIntegral = 4 };
 
+// One unit of work of the batched-toys launch.
+struct ToyItem {
+  int toy;
+  int is_data;      // 1: toy data events, 0: normalisation events
+  int64_t start, end;
+  int row;          // partial row written
+};
+
+struct ToyArgs {
+  const void* data;          // all toys' data events, toy t at [offsets[t], offsets[t+1])
+  const void* norm;          // shared normalisation sample
+  int64_t n_data, n_norm;    // total toy events, normalisation events
+  const int64_t* offsets;    // n_toys + 1 (device)
+  int n_toys;
+  const ToyItem* items;      // n_items (device), normalisation items first
+  int n_items;
+  unsigned int* queue;       // next item (zero before the launch)
+  int rows_per_toy;          // toy t owns rows [t * rows_per_toy, ...)
+  int norm_chunks;           // ... of which the first norm_chunks are normalisation rows
+  const int* data_rows;      // number of data rows of each toy (device)
+  const double* coef;        // n_toys blocks of coef_size() doubles
+  const float* coef32;       // n_toys blocks of coef32_size() floats
+  const double* lu;
+  double* partials;
+  double* out;               // n_toys blocks of 1 + P doubles
+  int* flags;
+  const void* basis_data;    // cached basis of the toy events or null
+  const void* basis_norm;    // cached basis of the normalisation sample or null
+  Model model;
+};
+
+// Spline setup for n_sets parameter vectors (params[s*P ...]) into
+// coef + s*coef_size and coef32 + s*coef32_size.
 void launch_prepare(const Model& m, const double* params, const double* lu, double* coef,
-                    float* coef32, cudaStream_t stream);
+                    float* coef32, cudaStream_t stream, int n_sets = 1);
+cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int grid,
+                        cudaStream_t stream);
+int toys_blocks_per_sm(int compute_f32, int ev_f32);
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t stream);
 // Cached Breit-Wigner basis of n events: out[r * n + i] = B_r (FP64 form) or

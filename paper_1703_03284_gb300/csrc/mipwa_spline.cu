@@ -19,6 +19,10 @@ __global__ void prepare_kernel(const Model m, const double* __restrict__ params,
                                const double* __restrict__ lu, double* __restrict__ coef,
                                float* __restrict__ coef32) {
   const int n_res = m.n_res, N = m.kn.n;
+  // block b serves parameter set b
+  params += (size_t)blockIdx.x * (2 * n_res + 2 * N);
+  coef += (size_t)blockIdx.x * coef_size(N, n_res);
+  coef32 += (size_t)blockIdx.x * coef32_size(N, n_res);
   __shared__ double M[2][kMaxKnots];
   const int nseg = N - 1, mm = N - 2;
   const double* h = lu;
@@ -80,8 +84,8 @@ __global__ void prepare_kernel(const Model m, const double* __restrict__ params,
 }
 
 void launch_prepare(const Model& m, const double* params, const double* lu, double* coef,
-                    float* coef32, cudaStream_t st) {
-  prepare_kernel<<<1, 64, 0, st>>>(m, params, lu, coef, coef32);
+                    float* coef32, cudaStream_t st, int n_sets) {
+  prepare_kernel<<<n_sets, 64, 0, st>>>(m, params, lu, coef, coef32);
 }
 
 }  // namespace mipwa
