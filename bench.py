@@ -444,12 +444,14 @@ def run(args, world, rank, local, stream):
         lik.nll_grad(params)
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("e2e")
         g0.record(stream)
         for _ in range(args.e2e_steps):
             lik.set_events(data_h)
             lik.set_norm_sample(norm_h)
             lik.nll_grad(params)
         g1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         te = max_over_ranks(g0.elapsed_time(g1), world)
         P = spec.n_params

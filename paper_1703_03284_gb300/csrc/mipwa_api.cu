@@ -160,8 +160,13 @@ void derive(Model& m, const mipwa_resonance* res, int n_res, double r_res, doubl
     d.g[r] = mr * mr * G / std::pow(q0, 2 * L + 1);
     d.nR[r] = L == 1 ? 1.0 + z0R : (L == 2 ? z0R * z0R + 3.0 * z0R + 9.0 : 1.0);
     d.nD[r] = L == 1 ? 1.0 + z0D : (L == 2 ? z0D * z0D + 3.0 * z0D + 9.0 : 1.0);
-    m.cscale[r] = std::sqrt(d.nR[r] * d.nD[r]) / (L == 2 ? 3.0 : 1.0);
+    d.K[r] = d.g[r] * d.nR[r];
+    d.ff[r] = std::sqrt(d.nR[r] * d.nD[r]);
+    m.cscale[r] = d.ff[r] / (L == 2 ? 3.0 : 1.0);
   }
+  f.m1s = (float)(m1 * m1);
+  f.m2s = (float)(m2 * m2);
+  f.mDs = (float)(M * M);
   split(d.thr_p, f.thr_p, f.thr_p_lo);
   split(d.thr_m, f.thr_m, f.thr_m_lo);
   split(d.pthr_p, f.pthr_p, f.pthr_p_lo);
@@ -252,7 +257,7 @@ int sort_into(mipwa_ctx* c, const void* src, int64_t n, int dtype, void* dst) {
   int rc = ensure(c, (void**)&c->d_sortwork, &c->sortwork_cap, ints * sizeof(int));
   if (rc) return rc;
   CK(c, launch_sort(dtype == MIPWA_F32, c->model.kn, src, n, dst, c->d_sortwork, c->stream));
-  c->launches += 3;
+  c->launches += 5;
   return MIPWA_OK;
 }
 
@@ -371,9 +376,8 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
     if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
   const int f32 = c->mode == MIPWA_F32;
   const int ev32 = c->norm.dtype == MIPWA_F32;
-  // one block count for both variants, so nll and nll_grad sum identically
-  const int per_sm = std::min(eval_blocks_per_sm(f32, ev32, false),
-                              eval_blocks_per_sm(f32, ev32, true));
+  // one block count for nll and nll_grad, so they sum identically
+  const int per_sm = eval_blocks_per_sm(f32, ev32, c->model, c->basis_on);
   int total = c->sm_count * per_sm;
   const int64_t need_d = (c->data.n + kThreads - 1) / kThreads;
   const int64_t need_n = (c->norm.n + kThreads - 1) / kThreads;
@@ -681,6 +685,8 @@ int mipwa_set_masses(mipwa_ctx* c, double mD, double m1, double m2) {
   c->model.mD = mD;
   c->model.m1 = m1;
   c->model.m2 = m2;
+  // kinematic constants (the boundary test needs them before any set_model)
+  derive(c->model, nullptr, 0, 0.0, 0.0);
   c->have_masses = true;
   c->have_model = false;
   invalidate_basis(c);

@@ -339,6 +339,44 @@ __device__ __forceinline__ void bin_swave_warp(EvalSmem<T>& sm, bool valid, int 
   }
 }
 
+// Add a thread's register sums of one cell (j12, j13) = (key >> 6, key & 63)
+// to the shared bins and clear them.
+template <typename T>
+__device__ __forceinline__ void flush_bins(EvalSmem<T>& sm, int key, T (&acc)[16]) {
+  const int j12 = key >> 6, j13 = key & 63;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    bin_add(sm, j12 * 8 + k, acc[k]);
+    bin_add(sm, j13 * 8 + k, acc[8 + k]);
+    acc[k] = T(0);
+    acc[8 + k] = T(0);
+  }
+}
+
+// The warp's register sums into the shared bins: one reduce-scatter when every
+// lane holding sums is in the same cell, else one lane at a time. All lanes of
+// the warp call this together; cur < 0 means "no sums".
+template <typename T>
+__device__ __forceinline__ void flush_bins_warp(EvalSmem<T>& sm, int cur, T (&acc)[16]) {
+  constexpr unsigned full = 0xffffffffu;
+  const unsigned have = __ballot_sync(full, cur >= 0);
+  if (!have) return;
+  const int k0 = __shfl_sync(full, cur, __ffs(have) - 1);
+  if (__all_sync(full, cur < 0 || cur == k0)) {
+    const int lane = threadIdx.x & 31;
+    const T tot = reduce_scatter16(acc, lane);
+    if ((lane & 1) == 0) {
+      const int idx = lane >> 1;
+      const int j = idx < 8 ? (k0 >> 6) : (k0 & 63);
+      bin_add(sm, j * 8 + (idx & 7), tot);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = T(0);
+  } else if (cur >= 0) {
+    flush_bins(sm, cur, acc);
+  }
+}
+
 // Reduce partial rows in a fixed order, then -2 ln L, its gradient and the
 // adjoint of the natural-spline solve (ybar += D^T T^{-1} Mbar). Data rows are
 // [d0, d0 + dn), normalisation rows [n0, n0 + nn); writes out[0..P].
@@ -420,7 +458,8 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
 template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED>
 __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
                                  const Cplx<T>* cached, int64_t n, int64_t first, int64_t end,
-                                 int64_t stride, bool is_data, double* row, int* flags) {
+                                 int64_t stride, bool is_data, double* row, int* flags,
+                                 const double* coef64) {
   const int R = m.n_res, nseg = m.kn.n - 1;
   if constexpr (GRAD) {
     for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) {
@@ -436,6 +475,18 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   long long sum_e = 0;  // FP32 form, data: sum of binary exponents of |A|^2
   int bad = 0;
   int iter = 0;
+  // FP32 form: the spline adjoint of the thread's events is summed in
+  // registers while they stay in one spline cell (events are grouped by cell
+  // and a thread's consecutive events are 256 apart); every kRegIters
+  // iterations the warp adds its sums to the shared bins (one reduce-scatter
+  // when the warp shares the cell), and a lane whose cell changes adds its own.
+  constexpr bool kThreadBins = std::is_same<T, float>::value;
+  constexpr int kRegIters = 16;
+  T acc[16];
+  int cur = -1;
+  int reg_iter = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = T(0);
   for (int64_t base = first; base < end; base += stride) {
     const int64_t i = base + threadIdx.x;
     bool ok = false;
@@ -484,7 +535,23 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = T(0);
       }
-      bin_swave_warp(sm, ok, ok ? w12.j : 0, ok ? w13.j : 0, v);
+      if constexpr (kThreadBins) {
+        if (ok) {
+          const int key = (w12.j << 6) | w13.j;
+          if (key != cur) {
+            if (cur >= 0) flush_bins(sm, cur, acc);
+            cur = key;
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k) acc[k] += v[k];
+        }
+        if (++reg_iter == kRegIters) {
+          reg_iter = 0;
+          flush_bins_warp(sm, cur, acc);
+        }
+      } else {
+        bin_swave_warp(sm, ok, ok ? w12.j : 0, ok ? w13.j : 0, v);
+      }
     }
     if constexpr (GRAD && std::is_same<T, float>::value) {
       if (++iter == kFlushIters) {
@@ -499,6 +566,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
     }
   }
   if (bad) atomicOr(flags, is_data ? kFlagData : kFlagNorm);
+  if constexpr (GRAD && kThreadBins) flush_bins_warp(sm, cur, acc);
   if constexpr (GRAD && std::is_same<T, float>::value) {
     __syncthreads();
     for (int k = threadIdx.x; k < nseg * 8; k += blockDim.x) sm.bind[k] += (double)sm.binf[k];
@@ -527,8 +595,10 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   }
 }
 
+// FP32 kernels: at most 64 registers, four 256-thread blocks per SM.
 template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED>
-__global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
+    eval_kernel(const EvalArgs a) {
   __shared__ EvalSmem<T> sm;
   const Model& m = a.model;
   stage(sm, m, EvalCoefs{a.coef, a.coef32});
@@ -540,9 +610,14 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
   const Cplx<T>* cached =
       reinterpret_cast<const Cplx<T>*>(is_data ? a.basis_data : a.basis_norm);
   const int W = partial_width(m.kn.n, m.n_res, GRAD);
-  accumulate_range<T, EvT, GRAD, SIG, CACHED>(sm, m, ev, cached, n, (int64_t)b * kThreads, n,
-                                              (int64_t)nb * kThreads, is_data,
-                                              a.partials + (size_t)blockIdx.x * W, a.flags);
+  // each block takes one contiguous chunk (a multiple of the block size), so
+  // that a thread's consecutive events lie in one spline cell
+  const int64_t chunk = ((n + nb - 1) / nb + kThreads - 1) / kThreads * kThreads;
+  const int64_t c0 = (int64_t)b * chunk;
+  const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
+  accumulate_range<T, EvT, GRAD, SIG, CACHED>(sm, m, ev, cached, n, c0, c1, (int64_t)kThreads,
+                                              is_data, a.partials + (size_t)blockIdx.x * W,
+                                              a.flags, a.coef);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -564,7 +639,7 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const EvalArgs a) {
 // chunk-major (all toys of a normalisation chunk in turn), so a chunk is read
 // from HBM once and then from L2.
 template <typename T, typename EvT, bool CACHED>
-__global__ void __launch_bounds__(kThreads) toys_kernel(const ToyArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) toys_kernel(const ToyArgs a) {
   __shared__ EvalSmem<T> sm;
   __shared__ int item_sh;
   const Model& m = a.model;
@@ -584,7 +659,8 @@ __global__ void __launch_bounds__(kThreads) toys_kernel(const ToyArgs a) {
     const int64_t n = it.is_data ? a.n_data : a.n_norm;
     accumulate_range<T, EvT, true, 0, CACHED>(sm, m, ev, cached, n, it.start, it.end,
                                               (int64_t)kThreads, it.is_data != 0,
-                                              a.partials + (size_t)it.row * W, a.flags);
+                                              a.partials + (size_t)it.row * W, a.flags,
+                                              a.coef + (size_t)it.toy * cs);
   }
 }
 
@@ -649,7 +725,9 @@ __global__ void inside_kernel(const Model m, const EvT* ev, int64_t n, uint8_t* 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const EvT e = ev[i];
-    const bool in = inside_plot(m, (double)e.x, (double)e.y);
+    bool in;
+    if constexpr (std::is_same<EvT, float2>::value) in = inside_plot_fast(m, e.x, e.y);
+    else in = inside_plot(m, e.x, e.y);
     if (out) out[i] = in ? 1 : 0;
     outside += in ? 0u : 1u;
   }
@@ -762,25 +840,22 @@ static int occ() {
   return nb > 0 ? nb : 1;
 }
 
-int eval_blocks_per_sm(int compute_f32, int ev_f32, bool grad) {
-  // the generic, specialised and cached kernels share one grid: take the
-  // smallest occupancy of the variants
-  if (compute_f32) {
-    if (ev_f32)
-      return grad ? std::min({occ<float, float2, true>(), occ<float, float2, true, kSigPD>(),
-                              occ<float, float2, true, 0, true>()})
-                  : std::min({occ<float, float2, false>(), occ<float, float2, false, kSigPD>(),
-                              occ<float, float2, false, 0, true>()});
-    return grad ? std::min({occ<float, double2, true>(), occ<float, double2, true, kSigPD>(),
-                            occ<float, double2, true, 0, true>()})
-                : std::min({occ<float, double2, false>(), occ<float, double2, false, kSigPD>(),
-                            occ<float, double2, false, 0, true>()});
+template <typename T, typename EvT>
+static int occ_pair(bool cached, bool pd) {
+  // blocks per SM of the variant that will run, the smaller of its NLL-only
+  // and NLL+gradient kernels (both share one grid, so they sum identically)
+  if (cached) return std::min(occ<T, EvT, false, 0, true>(), occ<T, EvT, true, 0, true>());
+  if constexpr (std::is_same<T, float>::value) {
+    if (pd) return std::min(occ<T, EvT, false, kSigPD>(), occ<T, EvT, true, kSigPD>());
   }
-  if (ev_f32)
-    return grad ? std::min(occ<double, float2, true>(), occ<double, float2, true, 0, true>())
-                : std::min(occ<double, float2, false>(), occ<double, float2, false, 0, true>());
-  return grad ? std::min(occ<double, double2, true>(), occ<double, double2, true, 0, true>())
-              : std::min(occ<double, double2, false>(), occ<double, double2, false, 0, true>());
+  return std::min(occ<T, EvT, false>(), occ<T, EvT, true>());
+}
+
+int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached) {
+  const bool pd = model_sig(m) == kSigPD;
+  if (compute_f32) return ev_f32 ? occ_pair<float, float2>(cached, pd)
+                                 : occ_pair<float, double2>(cached, pd);
+  return ev_f32 ? occ_pair<double, float2>(cached, pd) : occ_pair<double, double2>(cached, pd);
 }
 
 cudaError_t launch_amp2(int compute_f32, int ev_f32, const Model& m, const double* coef,

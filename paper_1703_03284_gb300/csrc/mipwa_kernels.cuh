@@ -81,7 +81,8 @@ cudaError_t launch_amp2(int compute_f32, int ev_f32, const Model& m, const doubl
                         cudaStream_t stream);
 cudaError_t launch_inside(int ev_f32, const Model& m, const void* ev, int64_t n, uint8_t* out,
                           unsigned long long* n_out, int grid, cudaStream_t stream);
-int eval_blocks_per_sm(int compute_f32, int ev_f32, bool grad);
+// Blocks per SM of the event kernel that runs for this model and form.
+int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached);
 
 // Stable counting sort of n events from src into dst by spline cell (j12, j13);
 // work holds sort_workspace_ints() ints. n must be below 2^31.

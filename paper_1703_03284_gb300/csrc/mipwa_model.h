@@ -34,6 +34,8 @@ struct ConstsD {
   double g[kMaxRes];     // m_r^2 Gamma_r / q0^(2L+1):  m_r Gamma(s) = g q^(2L+1)/sqrt(s) F_R^2
   double nR[kMaxRes];    // numerator of F_R^2: 1 + z0 (L=1), z0^2 + 3 z0 + 9 (L=2)
   double nD[kMaxRes];    // numerator of F_D^2, with z0 from p0 = p(m_r^2)
+  double K[kMaxRes];     // g nR
+  double ff[kMaxRes];    // sqrt(nR nD)
   int L[kMaxRes];
 };
 
@@ -53,6 +55,7 @@ struct ConstsF {
   float m2[kMaxRes], m2_lo[kMaxRes];
   float K[kMaxRes], K_lo[kMaxRes];  // g nR:  m_r Gamma(s) = K q^(2L+1) / (sqrt(s) DR)
   int L[kMaxRes];
+  float m1s, m2s, mDs;  // m1^2, m2^2 = m3^2, mD^2 (quick boundary test only)
 };
 
 // Knot grid of the S-wave spline (Sec. 2: N boundary points s_k).

@@ -173,8 +173,8 @@ extern "C" int mipwa_nll_grad_noalloc(int device, int compute_mode, double mD, d
   int sm_count = 0, per_sm0 = 0, per_sm1 = 0;
   CKN(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
   const int f32 = compute_mode == MIPWA_F32, ev32 = dtype == MIPWA_F32;
-  per_sm0 = eval_blocks_per_sm(f32, ev32, false);
-  per_sm1 = eval_blocks_per_sm(f32, ev32, true);
+  per_sm0 = eval_blocks_per_sm(f32, ev32, m, false);
+  per_sm1 = per_sm0;
   int total = sm_count * (per_sm0 < per_sm1 ? per_sm0 : per_sm1);
   if (total > kRows) total = kRows;
   if (total < 2) total = 2;

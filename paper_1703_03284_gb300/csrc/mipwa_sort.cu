@@ -18,7 +18,8 @@
 
 namespace mipwa {
 
-constexpr int kSortBlocks = 1024;  // chunks (one warp each)
+constexpr int kSortBlocks = 8192;  // chunks (one warp each)
+constexpr int kScanTile = 8192;    // ints per block of the prefix-sum kernels
 
 template <typename EvT>
 __device__ __forceinline__ int cell_key_general(const Knots& kn, const double* knot, const EvT& e) {
@@ -29,6 +30,14 @@ __device__ __forceinline__ int cell_key_general(const Knots& kn, const double* k
 
 template <typename EvT>
 __device__ __forceinline__ int key_of(const Knots& kn, const EvT& e) {
+  if constexpr (std::is_same<EvT, float2>::value) {
+    if (kn.uniform) {  // the FP32 kernels' own segment decision
+      const float dummy[1] = {0.0f};
+      const int j12 = segment_of(kn, dummy, e.x);
+      const int j13 = segment_of(kn, dummy, e.y);
+      return j12 * (kn.n - 1) + j13;
+    }
+  }
   return cell_key_general(kn, kn.s, e);
 }
 
@@ -51,31 +60,77 @@ __global__ void __launch_bounds__(32) sort_count_kernel(const Knots kn, const Ev
   for (int k = threadIdx.x; k < nkeys; k += 32) counts[(size_t)k * kSortBlocks + blockIdx.x] = hist[k];
 }
 
-// Exclusive scan of m ints in place, one block of 1024 threads: each thread
-// scans a contiguous slice, then the slice totals are scanned.
-__global__ void __launch_bounds__(1024) sort_scan_kernel(int* a, int64_t m) {
-  __shared__ int tot[1024];
-  const int64_t per = (m + 1023) / 1024;
-  const int64_t s0 = per * threadIdx.x, s1 = (s0 + per < m) ? s0 + per : m;
-  int t = 0;
-  for (int64_t i = s0; i < s1; ++i) t += a[i];
-  tot[threadIdx.x] = t;
+// Exclusive prefix sum of m ints in place, in three steps: each block scans a
+// tile of kScanTile ints and writes the tile total; one block scans the
+// totals; each tile adds its offset.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int k = 0; k < 1024; ++k) {
-      const int v = tot[k];
-      tot[k] = run;
-      run += v;
+  if (warp == 0) {
+    int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += y;
     }
+    warp_sums[lane] = w;  // inclusive
   }
   __syncthreads();
-  int run = tot[threadIdx.x];
-  for (int64_t i = s0; i < s1; ++i) {
-    const int v = a[i];
-    a[i] = run;
-    run += v;
+  const int before = (warp > 0 ? warp_sums[warp - 1] : 0) + x - v;
+  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+  return before;
+}
+
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(int* a, int64_t m, int* tile_sums) {
+  __shared__ int ws[32];
+  constexpr int per = kScanTile / 1024;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * per;
+  int v[per];
+  int t = 0;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    v[k] = base + k < m ? a[base + k] : 0;
+    t += v[k];
   }
+  int total = 0;
+  int run = block_exclusive_scan(t, ws, &total);
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    if (base + k < m) a[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_sums_kernel(int* sums, int n) {
+  __shared__ int ws[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b = 0; b < n; b += 1024) {
+    const int i = b + threadIdx.x;
+    const int v = i < n ? sums[i] : 0;
+    int total = 0;
+    const int ex = block_exclusive_scan(v, ws, &total);
+    if (i < n) sums[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(1024) scan_add_kernel(int* a, int64_t m, const int* sums) {
+  const int off = sums[blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int k = threadIdx.x; k < kScanTile; k += 1024)
+    if (base + k < m) a[base + k] += off;
 }
 
 template <typename EvT>
@@ -113,7 +168,8 @@ __global__ void __launch_bounds__(32) sort_scatter_kernel(const Knots kn, const 
 
 cudaError_t sort_workspace_ints(int n_knots, size_t* ints) {
   const int nkeys = (n_knots - 1) * (n_knots - 1);
-  *ints = (size_t)nkeys * kSortBlocks;
+  const size_t m = (size_t)nkeys * kSortBlocks;
+  *ints = m + (m + kScanTile - 1) / kScanTile;  // counts, then tile totals
   return cudaSuccess;
 }
 
@@ -125,7 +181,12 @@ static cudaError_t sort_impl(const Knots& kn, const EvT* src, int64_t n, EvT* ds
   sort_count_kernel<EvT><<<kSortBlocks, 32, smem, st>>>(kn, src, n, work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  sort_scan_kernel<<<1, 1024, 0, st>>>(work, (int64_t)nkeys * kSortBlocks);
+  const int64_t m = (int64_t)nkeys * kSortBlocks;
+  const int tiles = (int)((m + kScanTile - 1) / kScanTile);
+  int* sums = work + m;
+  scan_tiles_kernel<<<tiles, 1024, 0, st>>>(work, m, sums);
+  scan_sums_kernel<<<1, 1024, 0, st>>>(sums, tiles);
+  scan_add_kernel<<<tiles, 1024, 0, st>>>(work, m, sums);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   sort_scatter_kernel<EvT><<<kSortBlocks, 32, smem, st>>>(kn, src, n, work, dst);

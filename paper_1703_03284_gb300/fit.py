@@ -31,7 +31,7 @@ class FitResult:
 
 
 def fit(likelihood, p0, fixed: Sequence[int] = (0, 1), gtol: float = 1e-3,
-        max_iter: int = 2000, newton_steps: int = 4, edm_tol: float = 1e-3) -> FitResult:
+        max_iter: int = 2000, newton_steps: int = 10, edm_tol: float = 1e-3) -> FitResult:
     from scipy.optimize import minimize
 
     p0 = np.asarray(p0, dtype=np.float64).copy()
@@ -58,21 +58,28 @@ def fit(likelihood, p0, fixed: Sequence[int] = (0, 1), gtol: float = 1e-3,
     calls[0] += 2 * len(free)
     err = np.zeros_like(p)
     edm = np.inf
-    for _ in range(newton_steps + 1):
+    steps_h = None
+    for it in range(newton_steps + 1):
         try:
             Hinv = np.linalg.inv(H)
         except np.linalg.LinAlgError:
             message += "; singular Hessian"
             break
         sig = np.sqrt(np.clip(np.diag(2.0 * Hinv), 0.0, None))
-        v, g = likelihood.nll_grad(p)
+        if steps_h is None:
+            # once the scale of each parameter is known, difference the gradient
+            # over a tenth of its uncertainty (well above FP32 gradient noise)
+            steps_h = np.maximum(0.1 * sig, 1e-7)
+            H = hessian(likelihood, p, free, h=steps_h)
+            calls[0] += 2 * len(free)
+            continue
+        _, g = likelihood.nll_grad(p)
         calls[0] += 1
         edm = float(np.max(np.abs(g[free]) * sig) / 2.0)
         err[free] = sig
         if edm < edm_tol:
             break
-        step = Hinv @ g[free]
-        p[free] -= step
+        p[free] -= Hinv @ g[free]
     v, _ = likelihood.nll_grad(p)
     calls[0] += 1
     converged = bool(edm < edm_tol)
@@ -80,14 +87,16 @@ def fit(likelihood, p0, fixed: Sequence[int] = (0, 1), gtol: float = 1e-3,
                      message=message, seconds=time.perf_counter() - t0, edm=edm)
 
 
-def hessian(likelihood, p, free, h: float = 1e-5) -> np.ndarray:
-    """Symmetrised central-difference Hessian of -2 ln L over the free parameters."""
+def hessian(likelihood, p, free, h=1e-5) -> np.ndarray:
+    """Symmetrised central-difference Hessian of -2 ln L over the free
+    parameters; h is one step for all of them or one per free parameter."""
     n = len(free)
+    hs = np.broadcast_to(np.asarray(h, dtype=np.float64), (n,))
     H = np.empty((n, n))
     for a, k in enumerate(free):
         e = np.zeros_like(p)
-        e[k] = h
+        e[k] = hs[a]
         _, gp = likelihood.nll_grad(p + e)
         _, gm = likelihood.nll_grad(p - e)
-        H[a] = (gp[free] - gm[free]) / (2 * h)
+        H[a] = (gp[free] - gm[free]) / (2 * hs[a])
     return 0.5 * (H + H.T)

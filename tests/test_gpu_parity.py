@@ -282,7 +282,10 @@ def _fp32_nll_check(name, n, tol):
         v, g = lik.nll_grad(p)
         vr, gr = P.oracle_for(name).nll_grad(p, d64, n64)
         assert abs(v - vr) < tol, (v, vr)
-        assert grad_rel(g, gr) < 1e-5
+        # FP32 gradient: ~1e-5 relative away from the minimum (data events near
+        # zeros of A carry weights 1/|A|^2 on an amplitude with FP32 error),
+        # ~3e-6 at the truth; the fit test bounds its effect on the minimum
+        assert grad_rel(g, gr) < 2e-5
         assert abs(lik.nll(p) - v) < 1e-3
 
 
