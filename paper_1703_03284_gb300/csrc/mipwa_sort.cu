@@ -7,8 +7,12 @@
 // spline adjoint can be reduced across the warp before it is binned.
 //
 // The sort is a stable counting sort (deterministic for a given input):
-//   1. count:   each block counts the keys of its contiguous chunk;
-//   2. scan:    exclusive prefix sum in (key, block) order;
+//   1. count:   each block counts the keys of its contiguous chunk into its
+//               own row of a [block][key] table;
+//   2. offsets: the table becomes, in place, each (block, key)'s first output
+//               position: all events of lower keys, plus the events of the
+//               same key in earlier blocks (column sums over groups of
+//               blocks, one scan over keys, then the running sums per group);
 //   3. scatter: each block walks its chunk in order, one warp at a time, and
 //               places each event at its key's running offset.
 #include <cuda_runtime.h>
@@ -18,8 +22,7 @@
 
 namespace mipwa {
 
-constexpr int kSortBlocks = 8192;  // chunks (one warp each)
-constexpr int kScanTile = 8192;    // ints per block of the prefix-sum kernels
+constexpr int kSortBlocks = 8192;  // chunks (one warp each); a multiple of kGroup
 
 template <typename EvT>
 __device__ __forceinline__ int cell_key_general(const Knots& kn, const double* knot, const EvT& e) {
@@ -49,7 +52,7 @@ __host__ __device__ inline int64_t chunk_begin(int64_t n, int b) {
 
 template <typename EvT>
 __global__ void __launch_bounds__(32) sort_count_kernel(const Knots kn, const EvT* ev, int64_t n,
-                                                        int* counts /* [nkeys][kSortBlocks] */) {
+                                                        int* counts /* [kSortBlocks][nkeys] */) {
   extern __shared__ int hist[];
   const int nkeys = (kn.n - 1) * (kn.n - 1);
   for (int k = threadIdx.x; k < nkeys; k += 32) hist[k] = 0;
@@ -57,80 +60,83 @@ __global__ void __launch_bounds__(32) sort_count_kernel(const Knots kn, const Ev
   const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
   for (int64_t i = b0 + threadIdx.x; i < b1; i += 32) atomicAdd(&hist[key_of(kn, ev[i])], 1);
   __syncwarp();
-  for (int k = threadIdx.x; k < nkeys; k += 32) counts[(size_t)k * kSortBlocks + blockIdx.x] = hist[k];
+  for (int k = threadIdx.x; k < nkeys; k += 32) counts[(size_t)blockIdx.x * nkeys + k] = hist[k];
 }
 
-// Exclusive prefix sum of m ints in place, in three steps: each block scans a
-// tile of kScanTile ints and writes the tile total; one block scans the
-// totals; each tile adds its offset.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, off);
-    if (lane >= off) x += y;
-  }
-  if (lane == 31) warp_sums[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, off);
-      if (lane >= off) w += y;
-    }
-    warp_sums[lane] = w;  // inclusive
-  }
-  __syncthreads();
-  const int before = (warp > 0 ? warp_sums[warp - 1] : 0) + x - v;
-  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
-  return before;
-}
+constexpr int kGroup = 64;                        // blocks per column-sum group
+constexpr int kGroups = kSortBlocks / kGroup;     // 128
 
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(int* a, int64_t m, int* tile_sums) {
-  __shared__ int ws[32];
-  constexpr int per = kScanTile / 1024;
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * per;
-  int v[per];
+// group_sum[g][k] = sum of counts[b][k] over the blocks b of group g.
+__global__ void __launch_bounds__(256) sort_group_sums(const int* counts, int nkeys, int* group_sum) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (k >= nkeys) return;
   int t = 0;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    v[k] = base + k < m ? a[base + k] : 0;
-    t += v[k];
-  }
-  int total = 0;
-  int run = block_exclusive_scan(t, ws, &total);
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    if (base + k < m) a[base + k] = run;
-    run += v[k];
-  }
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+  for (int b = g * kGroup; b < (g + 1) * kGroup; ++b) t += counts[(size_t)b * nkeys + k];
+  group_sum[(size_t)g * nkeys + k] = t;
 }
 
-__global__ void __launch_bounds__(1024) scan_sums_kernel(int* sums, int n) {
+// One block: per key, the exclusive scan of its group sums (in place) and its
+// total; then the exclusive scan of the totals over keys -> key_start.
+__global__ void __launch_bounds__(1024) sort_key_starts(int* group_sum, int nkeys, int* key_start) {
   __shared__ int ws[32];
   __shared__ int carry;
+  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) {
+    int run = 0;
+    for (int g = 0; g < kGroups; ++g) {
+      const int v = group_sum[(size_t)g * nkeys + k];
+      group_sum[(size_t)g * nkeys + k] = run;
+      run += v;
+    }
+    key_start[k] = run;  // total for now
+  }
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int b = 0; b < n; b += 1024) {
+  for (int b = 0; b < nkeys; b += 1024) {
     const int i = b + threadIdx.x;
-    const int v = i < n ? sums[i] : 0;
-    int total = 0;
-    const int ex = block_exclusive_scan(v, ws, &total);
-    if (i < n) sums[i] = carry + ex;
+    const int v = i < nkeys ? key_start[i] : 0;
+    // block-wide exclusive scan
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int w = ws[lane];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += y;
+      }
+      ws[lane] = w;
+    }
+    __syncthreads();
+    const int ex = (warp > 0 ? ws[warp - 1] : 0) + x - v;
+    const int total = ws[31];
+    __syncthreads();
+    if (i < nkeys) key_start[i] = carry + ex;
     __syncthreads();
     if (threadIdx.x == 0) carry += total;
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(1024) scan_add_kernel(int* a, int64_t m, const int* sums) {
-  const int off = sums[blockIdx.x];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  for (int k = threadIdx.x; k < kScanTile; k += 1024)
-    if (base + k < m) a[base + k] += off;
+// counts[b][k] -> key_start[k] + group prefix + running sum within the group.
+__global__ void __launch_bounds__(256) sort_offsets(int* counts, int nkeys, const int* group_sum,
+                                                    const int* key_start) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (k >= nkeys) return;
+  int run = key_start[k] + group_sum[(size_t)g * nkeys + k];
+  for (int b = g * kGroup; b < (g + 1) * kGroup; ++b) {
+    const int v = counts[(size_t)b * nkeys + k];
+    counts[(size_t)b * nkeys + k] = run;
+    run += v;
+  }
 }
 
 template <typename EvT>
@@ -139,7 +145,7 @@ __global__ void __launch_bounds__(32) sort_scatter_kernel(const Knots kn, const 
   extern __shared__ int cursor[];
   const int nkeys = (kn.n - 1) * (kn.n - 1);
   for (int k = threadIdx.x; k < nkeys; k += 32)
-    cursor[k] = offsets[(size_t)k * kSortBlocks + blockIdx.x];
+    cursor[k] = offsets[(size_t)blockIdx.x * nkeys + k];
   __syncwarp();
   const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
   const unsigned lane_lt = (1u << threadIdx.x) - 1u;
@@ -168,8 +174,8 @@ __global__ void __launch_bounds__(32) sort_scatter_kernel(const Knots kn, const 
 
 cudaError_t sort_workspace_ints(int n_knots, size_t* ints) {
   const int nkeys = (n_knots - 1) * (n_knots - 1);
-  const size_t m = (size_t)nkeys * kSortBlocks;
-  *ints = m + (m + kScanTile - 1) / kScanTile;  // counts, then tile totals
+  // counts [kSortBlocks][nkeys], group sums [kGroups][nkeys], key starts [nkeys]
+  *ints = (size_t)nkeys * (kSortBlocks + kGroups + 1);
   return cudaSuccess;
 }
 
@@ -181,12 +187,12 @@ static cudaError_t sort_impl(const Knots& kn, const EvT* src, int64_t n, EvT* ds
   sort_count_kernel<EvT><<<kSortBlocks, 32, smem, st>>>(kn, src, n, work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t m = (int64_t)nkeys * kSortBlocks;
-  const int tiles = (int)((m + kScanTile - 1) / kScanTile);
-  int* sums = work + m;
-  scan_tiles_kernel<<<tiles, 1024, 0, st>>>(work, m, sums);
-  scan_sums_kernel<<<1, 1024, 0, st>>>(sums, tiles);
-  scan_add_kernel<<<tiles, 1024, 0, st>>>(work, m, sums);
+  int* group_sum = work + (size_t)nkeys * kSortBlocks;
+  int* key_start = group_sum + (size_t)nkeys * kGroups;
+  const dim3 cgrid((nkeys + 255) / 256, kGroups);
+  sort_group_sums<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum);
+  sort_key_starts<<<1, 1024, 0, st>>>(group_sum, nkeys, key_start);
+  sort_offsets<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum, key_start);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   sort_scatter_kernel<EvT><<<kSortBlocks, 32, smem, st>>>(kn, src, n, work, dst);
