@@ -23,7 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
-import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -35,10 +35,12 @@ WORKLOAD = ("pipipi_n40_1e8_f32: D+->pi-pi+pi+, rho(770) P + f2(1270) D + 40-kno
             "(s12,s13)")
 
 # Algorithmic work per event of one NLL+gradient evaluation of this model
-# (2 resonances, one P- and one D-wave; counts in the design doc: add/sub/mul = 1,
-# fused multiply-add = 2, each division, square root, sine/cosine and log = 1).
-FLOPS_PER_EVENT_FWD = 211
-FLOPS_PER_EVENT_GRAD = 291
+# (2 resonances, one P- and one D-wave; add/sub/mul = 1, fused multiply-add = 2,
+# each division, square root, sine, cosine and log = 1). Forward: kinematics 24,
+# Zemach 18, Breit-Wigner terms 86, Bose combination 20, S-wave 42, |A|^2 and
+# reduction 5; gradient: c_r 20, spline adjoint 50, weights 1.5.
+FLOPS_PER_EVENT_FWD = 195
+FLOPS_PER_EVENT_GRAD = 267
 # Peaks from unit counts and the maximum SM clock (2070 MHz, 152 SMs):
 #   FP32: 128 lanes x 2 flop x 152 x 2.07 GHz;  FP64: 1.25 TFLOP/s (GB300 nominal).
 PEAK_FP32_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
@@ -67,7 +69,7 @@ TRAFFIC_PER_LAUNCH = 1.622e9
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-events", type=int, default=100_000_000,
@@ -78,51 +80,74 @@ def parse():
     ap.add_argument("--toys-steps", type=int, default=3)
     ap.add_argument("--n-toys", type=int, default=256)
     ap.add_argument("--toys-norm", type=int, default=10_000_000)
+    ap.add_argument("--paper-fit", type=int, default=1,
+                    help="run the Sec. 4 workload (K K K, 40 knots, 100K toy) as full fits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi every 200 ms in a child process; a reader thread stamps each
+    sample on arrival, and stop() keeps the samples that arrived between
+    begin() and end() (plus one sampling period), i.e. during the timed loop."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.2
 
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
-        self.path = None
+        self.rows = []
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.perf_counter(), line))
 
     def start(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", str(int(self.PERIOD_S * 1000))],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        deadline = time.perf_counter() + 5.0  # wait for the first sample
+        while not self.rows and time.perf_counter() < deadline and self.proc.poll() is None:
+            time.sleep(0.02)
+
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(self.PERIOD_S)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.thread.join(timeout=5)
         rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-                except ValueError:
-                    continue
-        os.unlink(self.path)
+        for t, line in self.rows:
+            if self.t0 is not None and not (self.t0 <= t <= self.t1 + self.PERIOD_S):
+                continue
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
         if not rows:
             return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -130,7 +155,7 @@ class ClockSampler:
                           if v.lower().startswith("active")})
         return {"sm_mhz": statistics.median(r[0] for r in rows),
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "timed_s": round(self.t1 - self.t0, 3)}
 
 
 # ------------------------------------------------------------- distributed
@@ -306,6 +331,57 @@ def toys_leg(args, stream, rank):
             "dtype": "f32 (cached basis, CUDA graph)"}
 
 
+# ------------------------------------------------------- the paper's own fit
+PAPER_FIT_SECONDS = {"Tesla K40c": 76, "GeForce GTX 980": 67, "GeForce GT 650M": 179,
+                     "2x Xeon E5-2680 v3, 24 threads": 50, "same, 1 thread": 791}
+
+
+def paper_fit_leg(rank):
+    """The workload of Sec. 4: D+ -> K- K+ K+ with the phi(1020) P-wave and a
+    40-knot K+K- S-wave, one 100K-event toy drawn from the model, fitted with
+    the normalisation on evenly spaced grids of 0.01, 0.004 and 0.001 GeV^2
+    (Fig. 2). Reports the wall time of each full fit (BFGS + Newton steps +
+    Hessian errors, FP64, as the paper's Table 1 reports fit times) and the
+    per-knot pulls (fit - input)/sigma of the magnitudes and phases."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1703_03284_gb300 import F32, F64, Likelihood
+    from paper_1703_03284_gb300.fit import fit
+
+    spec = synth.kkk(40)
+    truth = synth.true_params(spec)
+    dev = torch.cuda.current_device()
+    lik = Likelihood(dev, F64)
+    lik.set_spec(spec)
+    data = synth.accept_reject(spec, 100_000, lambda x: lik.amp2(truth, x), seed=42 + rank,
+                               device="cuda")
+    lik.set_events(data)
+    start = synth.perturbed_params(spec, 43, 0.02)
+    start[:2] = truth[:2]
+    out = []
+    for spacing in (0.01, 0.004, 0.001):
+        grid = synth.spacing_grid_in_plot(spec, spacing, lambda x: lik.inside(x).to(torch.float64),
+                                          device="cuda")
+        lik.set_norm_sample(grid)
+        for _ in range(3):
+            lik.nll_grad(start)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fit(lik, start, fixed=(0, 1))
+        dt = time.perf_counter() - t0
+        free = np.arange(2, spec.n_params)
+        pulls = (res.params[free] - truth[free]) / res.errors[free]
+        out.append({"grid_spacing_gev2": spacing, "norm_points": int(grid.shape[0]),
+                    "fit_seconds": dt, "nll_grad_calls": res.n_calls,
+                    "converged": res.converged, "edm": res.edm,
+                    "mean_abs_pull": float(np.mean(np.abs(pulls))),
+                    "max_abs_pull": float(np.max(np.abs(pulls)))})
+    return {"workload": "D+ -> K- K+ K+, phi(1020) P-wave + 40-knot S-wave, 100K toy events, FP64",
+            "fits": out, "paper_fit_seconds": PAPER_FIT_SECONDS}
+
+
 # ------------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -356,12 +432,14 @@ def run(args, world, rank, local, stream):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")
+    clocks.begin()
     e0.record(stream)
     for _ in range(args.steps):
         lik.nll_grad(params)
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
+    clocks.end()
     barrier(world)
     clk = clocks.stop()
     t_ms = max_over_ranks(e0.elapsed_time(e1), world)
@@ -466,6 +544,8 @@ def run(args, world, rank, local, stream):
         torch.cuda.empty_cache()
         toys = toys_leg(args, stream, rank)
 
+    paper = paper_fit_leg(rank) if args.paper_fit else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec, params)
@@ -480,7 +560,8 @@ def run(args, world, rank, local, stream):
                        "l2": "inputs (1.6 GB) larger than L2 (129 MB); no flush needed",
                        "parallelism": f"replicas x{world} (no collective)"},
             "roofline": roofline, "fp64_plain": fp64, "fp32_cached_basis": cached,
-            "batched_toys": toys, "e2e": e2e, "cpu_baseline": cpu,
+            "batched_toys": toys, "paper_workload_fit": paper, "e2e": e2e,
+            "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)
 

@@ -2,12 +2,20 @@
 of arXiv:1703.03284, Sec. 2), calling the library's NLL+gradient each step.
 
 Fixed parameters (by default Re c_0, Im c_0: the reference wave) are held at
-their start values. The fit is BFGS on the analytic gradient, followed by
-Newton steps with the Hessian of -2 ln L (central differences of the analytic
-gradient), which pin the minimum by the gradient alone: near the minimum the
-change of -2 ln L between nearby points is below its own rounding in FP32, so
-a line search on function values stalls there while the gradient stays exact
-to ~1e-6. Uncertainties: cov = 2 H^{-1}.
+their start values. The fit runs in three stages:
+
+1. a second-derivative estimate at the start point (central differences of the
+   analytic gradient), whose eigenvalues, taken in absolute value and floored,
+   whiten the free parameters, so that -2 ln L has roughly unit curvature in
+   every direction (the start-up estimate of a variable-metric minimiser);
+2. BFGS on the analytic gradient in the whitened coordinates;
+3. Newton steps with the Hessian of -2 ln L differenced over a tenth of each
+   parameter's uncertainty, which pin the minimum by the gradient alone: near
+   the minimum the change of -2 ln L between nearby points is below its own
+   rounding in FP32, so a line search on function values stalls there while
+   the gradient stays exact to ~1e-6.
+
+Uncertainties: cov = 2 H^{-1}.
 """
 from __future__ import annotations
 
@@ -50,15 +58,24 @@ def fit(likelihood, p0, fixed: Sequence[int] = (0, 1), gtol: float = 1e-3,
         return v, g[free]
 
     t0 = time.perf_counter()
-    res = minimize(fg, p0[free], jac=True, method="BFGS",
+    W = whitening(likelihood, p0, free)
+    calls[0] += 2 * len(free)
+
+    def fg_white(y):
+        v, g = fg(p0[free] + W @ y)
+        return v, W.T @ g
+
+    res = minimize(fg_white, np.zeros(len(free)), jac=True, method="BFGS",
                    options={"gtol": gtol, "maxiter": max_iter})
-    p = full(res.x)
+    p = full(p0[free] + W @ res.x)
     message = str(res.message)
-    H = hessian(likelihood, p, free)
+    # difference the gradient over a tenth of each parameter's uncertainty at
+    # the start (well above FP32 gradient noise): sigma^2 = 2 (W W^T)_kk
+    steps_h = np.maximum(0.1 * np.sqrt(2.0 * np.sum(W * W, axis=1)), 1e-7)
+    H = hessian(likelihood, p, free, h=steps_h)
     calls[0] += 2 * len(free)
     err = np.zeros_like(p)
     edm = np.inf
-    steps_h = None
     for it in range(newton_steps + 1):
         try:
             Hinv = np.linalg.inv(H)
@@ -66,13 +83,6 @@ def fit(likelihood, p0, fixed: Sequence[int] = (0, 1), gtol: float = 1e-3,
             message += "; singular Hessian"
             break
         sig = np.sqrt(np.clip(np.diag(2.0 * Hinv), 0.0, None))
-        if steps_h is None:
-            # once the scale of each parameter is known, difference the gradient
-            # over a tenth of its uncertainty (well above FP32 gradient noise)
-            steps_h = np.maximum(0.1 * sig, 1e-7)
-            H = hessian(likelihood, p, free, h=steps_h)
-            calls[0] += 2 * len(free)
-            continue
         _, g = likelihood.nll_grad(p)
         calls[0] += 1
         edm = float(np.max(np.abs(g[free]) * sig) / 2.0)
@@ -85,6 +95,19 @@ def fit(likelihood, p0, fixed: Sequence[int] = (0, 1), gtol: float = 1e-3,
     converged = bool(edm < edm_tol)
     return FitResult(params=p, nll=float(v), errors=err, n_calls=calls[0], converged=converged,
                      message=message, seconds=time.perf_counter() - t0, edm=edm)
+
+
+def whitening(likelihood, p, free, floor: float = 1e-6) -> np.ndarray:
+    """W with W^T H W ~ 1 for the second-derivative matrix H of -2 ln L at p:
+    W = V |Lambda|^{-1/2} from the eigen-decomposition of H, the eigenvalues
+    taken in absolute value (a start point need not lie where -2 ln L is
+    convex) and floored at `floor` times the largest one."""
+    h = 1e-4 * np.maximum(1.0, np.abs(p[free]))
+    H = hessian(likelihood, p, free, h=h)
+    lam, V = np.linalg.eigh(H)
+    lam = np.abs(lam)
+    lam = np.maximum(lam, floor * max(lam.max(), 1e-300))
+    return V / np.sqrt(lam)
 
 
 def hessian(likelihood, p, free, h=1e-5) -> np.ndarray:

@@ -94,9 +94,24 @@ def kpipi(n_knots: int) -> ModelSpec:
         knots=uniform_knots(lo, hi, n_knots))
 
 
+def kkk(n_knots: int = 40) -> ModelSpec:
+    """D+ -> K- K+ K+ (Sec. 4): phi(1020) P-wave + MIPWA K+K- S-wave with knots
+    over the whole m^2(K+K-) range. The phi mass and width are not in the paper;
+    these are the world-average values (1019.461 MeV, 4.249 MeV)."""
+    lo = (2 * M_K) ** 2
+    hi = (M_D - M_K) ** 2
+    return ModelSpec(name=f"kkk_n{n_knots}", mD=M_D, m1=M_K, m2=M_K,
+                     resonances=((1.019461, 0.004249, 1),),
+                     knots=uniform_knots(lo, hi, n_knots))
+
+
 def true_params(spec: ModelSpec) -> np.ndarray:
     """[Re c_0, Im c_0, ..., a_0..a_{N-1}, phi_0..phi_{N-1}]."""
-    c = [0.2 + 0.0j, 0.3 * complex(math.cos(1.0), math.sin(1.0))]
+    if spec.name.startswith("kkk"):
+        # c_phi = 0.06: the phi makes ~10 % of the rate, the S-wave the rest (Sec. 4)
+        c = [0.06 + 0.0j]
+    else:
+        c = [0.2 + 0.0j, 0.3 * complex(math.cos(1.0), math.sin(1.0))]
     c = (c + [0.1 + 0.0j] * spec.n_res)[: spec.n_res]
     n = spec.n_knots
     a = [1.0 + 0.5 * math.sin(k) for k in range(n)]
@@ -262,4 +277,4 @@ CONFIGS = {
 
 
 def model_for(kind: str, n_knots: int) -> ModelSpec:
-    return {"pipipi": pipipi, "kpipi": kpipi}[kind](n_knots)
+    return {"pipipi": pipipi, "kpipi": kpipi, "kkk": kkk}[kind](n_knots)

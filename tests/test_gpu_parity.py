@@ -64,7 +64,7 @@ def test_fp64_small_config(which):
     assert rel(lik.nll(p), v) < 1e-14
 
 
-@pytest.mark.parametrize("name", ["pipipi_n30", "pipipi_n40", "kpipi_n40"])
+@pytest.mark.parametrize("name", ["pipipi_n30", "pipipi_n40", "kpipi_n40", "kkk_n40"])
 def test_fp64_models(name):
     data, norm = P.data_sample(name, 20_000), P.uniform_sample(name, 30_000)
     spec = P.spec_by_name(name)
