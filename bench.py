@@ -344,10 +344,11 @@ def paper_fit_leg(rank):
     Hessian errors, FP64, as the paper's Table 1 reports fit times) and the
     per-knot pulls (fit - input)/sigma of the magnitudes and phases."""
     import numpy as np
+    import scipy.optimize  # noqa: F401  (imported here, outside the timed fits)
     import torch
 
     import synth
-    from paper_1703_03284_gb300 import F32, F64, Likelihood
+    from paper_1703_03284_gb300 import F64, Likelihood
     from paper_1703_03284_gb300.fit import fit
 
     spec = synth.kkk(40)
