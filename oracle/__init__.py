@@ -27,6 +27,8 @@ MAX_RES = 8
 MAX_KNOTS = 128
 
 OK, EINVAL, ENONPOS = 0, -1, -3
+# S-wave knot parametrisations: (a_k, phi_k) or (Re, Im) of the knot values
+SWAVE_FORMS = {"magphase": 0, "reim": 1}
 
 
 class OracleModel(ctypes.Structure):
@@ -44,6 +46,7 @@ class OracleModel(ctypes.Structure):
         ("knots", ctypes.c_double * MAX_KNOTS),
         ("r_res", ctypes.c_double),
         ("r_D", ctypes.c_double),
+        ("swave_form", ctypes.c_int),
     ]
 
 
@@ -113,7 +116,7 @@ def default_threads() -> int:
 def make_model(model) -> OracleModel:
     """Build the ctypes model from any object with the attributes of
     ``synth.ModelSpec`` (mD, m1, m2, resonances[(mass, width, spin)], knots,
-    r_res, r_D)."""
+    r_res, r_D, and optionally swave_form: "magphase" (default) or "reim")."""
     m = OracleModel()
     m.mD, m.m1, m.m2 = float(model.mD), float(model.m1), float(model.m2)
     res = list(model.resonances)
@@ -129,6 +132,10 @@ def make_model(model) -> OracleModel:
     for k, x in enumerate(knots):
         m.knots[k] = float(x)
     m.r_res, m.r_D = float(model.r_res), float(model.r_D)
+    form = getattr(model, "swave_form", "magphase")
+    if form not in SWAVE_FORMS:
+        raise ValueError(f"unknown S-wave form {form!r}")
+    m.swave_form = SWAVE_FORMS[form]
     return m
 
 

@@ -13,7 +13,9 @@
 //     Zemach tensors.
 //   * Sec. 2: MIPWA S-wave A0(s) = a0(s) exp(i phi0(s)), with (a_k, phi_k) at the N
 //     boundary points and a cubic spline in between (natural boundary conditions:
-//     magnitude and phase splined separately).
+//     magnitude and phase splined separately). The other reading of "a cubic
+//     spline in the complex plane" (form 1): the real and imaginary parts
+//     x_k + i y_k of the knot values splined separately, A0 = x(s) + i y(s).
 //   * Sec. 4: Bose symmetrisation along both m^2(h+h-) axes.
 //   * Sec. 2 / Sec. 4: unbinned -2 ln L with a normalisation integral taken as the
 //     mean of |A|^2 over a phase-space sample (evenly spaced grid or uniform MC).
@@ -50,6 +52,7 @@ typedef struct {
   int n_knots;                       // N >= 2 spline boundary points
   double knots[ORACLE_MAX_KNOTS];    // strictly increasing s_k (GeV^2)
   double r_res, r_D;                 // Blatt-Weisskopf radii (1/GeV)
+  int swave_form;                    // 0: magnitude/phase knots, 1: real/imaginary knots
 } oracle_model;
 
 enum { ORACLE_OK = 0, ORACLE_EINVAL = -1, ORACLE_ENONPOS = -3 };
@@ -196,8 +199,9 @@ static double spline_eval(int n, const double* x, const double* y, const double*
 struct Evaluator {
   const oracle_model* md;
   int R, N;
+  bool reim;                    // S-wave knots are (Re, Im) instead of (magnitude, phase)
   std::vector<cplx> c;          // BW coefficients c_r
-  std::vector<double> a, phi;   // knot magnitudes and phases
+  std::vector<double> a, phi;   // knot magnitudes and phases (form 1: real and imaginary parts)
   std::vector<double> Ma, Mphi; // their spline second derivatives
   // For the gradient: second derivatives of the spline through the unit vector e_k.
   std::vector<std::vector<double>> Munit;
@@ -205,6 +209,7 @@ struct Evaluator {
   Evaluator(const oracle_model* m, const double* params, bool want_unit) : md(m) {
     R = md->n_res;
     N = md->n_knots;
+    reim = md->swave_form == 1;
     c.resize(R);
     for (int r = 0; r < R; ++r) c[r] = cplx(params[2 * r], params[2 * r + 1]);
     a.assign(params + 2 * R, params + 2 * R + N);
@@ -229,9 +234,10 @@ struct Evaluator {
   }
 
   cplx swave(double s) const {
-    const double mag = spline_eval(N, md->knots, a.data(), Ma.data(), s);
-    const double ph = spline_eval(N, md->knots, phi.data(), Mphi.data(), s);
-    return mag * cplx(std::cos(ph), std::sin(ph));
+    const double u = spline_eval(N, md->knots, a.data(), Ma.data(), s);
+    const double v = spline_eval(N, md->knots, phi.data(), Mphi.data(), s);
+    if (reim) return cplx(u, v);
+    return u * cplx(std::cos(v), std::sin(v));
   }
 
   cplx amp(double s12, double s13) const {
@@ -242,6 +248,7 @@ struct Evaluator {
   }
 
   // d|A|^2/d(theta) for every parameter theta, written into g (length 2R+2N).
+  // With z = dA/d(theta), d|A|^2/d(theta) = 2 Re(conj(A) z).
   void amp2_grad(double s12, double s13, cplx A, double* g) const {
     for (int r = 0; r < R; ++r) {
       const cplx B = basis(r, s12, s13);
@@ -253,18 +260,25 @@ struct Evaluator {
     std::vector<double> e(N, 0.0);
     for (int ch = 0; ch < 2; ++ch) {
       const double s = ss[ch];
-      const double mag = spline_eval(N, md->knots, a.data(), Ma.data(), s);
-      const double ph = spline_eval(N, md->knots, phi.data(), Mphi.data(), s);
-      const cplx u(std::cos(ph), std::sin(ph));
-      // dA/da(s) = u ; dA/dphi(s) = i a(s) u
-      const double da = 2.0 * std::real(std::conj(A) * u);
-      const double dphi = 2.0 * std::real(std::conj(A) * cplx(0.0, 1.0) * mag * u);
+      // dA/du(s) and dA/dv(s) for the two splined functions u, v of this channel
+      cplx du, dv;
+      if (reim) {
+        du = cplx(1.0, 0.0);  // A0 = x + i y
+        dv = cplx(0.0, 1.0);
+      } else {
+        const double mag = spline_eval(N, md->knots, a.data(), Ma.data(), s);
+        const double ph = spline_eval(N, md->knots, phi.data(), Mphi.data(), s);
+        du = cplx(std::cos(ph), std::sin(ph));  // A0 = a e^{i phi}
+        dv = cplx(0.0, 1.0) * mag * du;
+      }
+      const double gu = 2.0 * std::real(std::conj(A) * du);
+      const double gv = 2.0 * std::real(std::conj(A) * dv);
       for (int k = 0; k < N; ++k) {
         e[k] = 1.0;
         const double w = spline_eval(N, md->knots, e.data(), Munit[k].data(), s);
         e[k] = 0.0;
-        g[2 * R + k] += da * w;
-        g[2 * R + N + k] += dphi * w;
+        g[2 * R + k] += gu * w;
+        g[2 * R + N + k] += gv * w;
       }
     }
   }
@@ -294,6 +308,7 @@ static int valid_model(const oracle_model* md) {
     if (!(md->knots[k] > md->knots[k - 1])) return 0;
   for (int r = 0; r < md->n_res; ++r)
     if (md->spin[r] < 0 || md->spin[r] > 2) return 0;
+  if (md->swave_form != 0 && md->swave_form != 1) return 0;
   return 1;
 }
 

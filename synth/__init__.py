@@ -48,6 +48,8 @@ class ModelSpec:
     r_res: float = 1.5
     r_D: float = 5.0
     fixed: tuple = (0, 1)  # parameter indices held fixed in fits (Re c_0, Im c_0)
+    # S-wave knot values: "magphase" = (a_k, phi_k), "reim" = (Re, Im) of a_k e^{i phi_k}
+    swave_form: str = "magphase"
 
     @property
     def n_res(self) -> int:
@@ -105,8 +107,16 @@ def kkk(n_knots: int = 40) -> ModelSpec:
                      knots=uniform_knots(lo, hi, n_knots))
 
 
+def as_reim(spec: ModelSpec) -> ModelSpec:
+    """The same decay model with the S-wave knot values taken as real and
+    imaginary parts (the complex-plane spline of Sec. 2 read literally)."""
+    return dataclasses.replace(spec, name=spec.name + "_reim", swave_form="reim")
+
+
 def true_params(spec: ModelSpec) -> np.ndarray:
-    """[Re c_0, Im c_0, ..., a_0..a_{N-1}, phi_0..phi_{N-1}]."""
+    """[Re c_0, Im c_0, ..., a_0..a_{N-1}, phi_0..phi_{N-1}]; for the Re/Im form
+    the knot block is [a_k cos phi_k..., a_k sin phi_k...] (the same complex
+    knot values)."""
     if spec.name.startswith("kkk"):
         # c_phi = 0.06: the phi makes ~10 % of the rate, the S-wave the rest (Sec. 4)
         c = [0.06 + 0.0j]
@@ -119,6 +129,9 @@ def true_params(spec: ModelSpec) -> np.ndarray:
     out = []
     for z in c:
         out += [z.real, z.imag]
+    if spec.swave_form == "reim":
+        a, phi = ([ak * math.cos(pk) for ak, pk in zip(a, phi)],
+                  [ak * math.sin(pk) for ak, pk in zip(a, phi)])
     return np.array(out + a + phi, dtype=np.float64)
 
 
@@ -276,5 +289,6 @@ CONFIGS = {
 }
 
 
-def model_for(kind: str, n_knots: int) -> ModelSpec:
-    return {"pipipi": pipipi, "kpipi": kpipi, "kkk": kkk}[kind](n_knots)
+def model_for(kind: str, n_knots: int, swave_form: str = "magphase") -> ModelSpec:
+    spec = {"pipipi": pipipi, "kpipi": kpipi, "kkk": kkk}[kind](n_knots)
+    return as_reim(spec) if swave_form == "reim" else spec

@@ -10,8 +10,13 @@ import synth
 
 
 def spec_by_name(name: str) -> synth.ModelSpec:
+    """"pipipi_n30" -> the 30-knot pi pi pi model; a "_reim" suffix selects the
+    Re/Im S-wave form of the same model."""
+    form = "magphase"
+    if name.endswith("_reim"):
+        name, form = name[: -len("_reim")], "reim"
     kind, n = name.split("_n")
-    return synth.model_for(kind, int(n))
+    return synth.model_for(kind, int(n), form)
 
 
 @functools.lru_cache(maxsize=None)

@@ -549,3 +549,112 @@ def test_oracle_reproduces_frozen_values():
             v, g = o.nll_grad(np.array(e["params"]), data, norm, threads=2)
             assert v == pytest.approx(e["nll"], rel=1e-12)
             np.testing.assert_allclose(g, e["grad"], rtol=1e-9, atol=1e-9 * np.abs(g).max())
+
+
+# ------------------------------------------------ Re/Im (complex-plane) spline
+REIM_SPECS = [synth.as_reim(synth.pipipi(10)), synth.as_reim(synth.kpipi(12))]
+
+
+@pytest.mark.parametrize("spec", [synth.pipipi(10), synth.kpipi(12)], ids=lambda s: s.name)
+def test_reim_equals_magphase_on_knots(spec):
+    """Both S-wave forms interpolate the same complex knot values: with
+    x_k + i y_k = a_k e^{i phi_k} and both invariants on knots, the amplitudes
+    agree exactly (to rounding)."""
+    o_mp, o_ri = oracle.Oracle(spec), oracle.Oracle(synth.as_reim(spec))
+    p = synth.perturbed_params(spec, 23)
+    R, N = spec.n_res, spec.n_knots
+    a, phi = p[2 * R:2 * R + N], p[2 * R + N:]
+    q = np.concatenate([p[:2 * R], a * np.cos(phi), a * np.sin(phi)])
+    k = np.asarray(spec.knots)
+    pts = np.array([(x, y) for x in k for y in k])
+    pts = pts[o_mp.inside(pts)]
+    assert len(pts) > 10
+    np.testing.assert_allclose(o_ri.amp(q, pts), o_mp.amp(p, pts), rtol=1e-13, atol=1e-13)
+    # between knots the two forms differ (different interpolants)
+    mid = np.array([[0.5 * (k[2] + k[3]), 0.5 * (k[4] + k[5])]])
+    assert abs(o_ri.amp(q, mid)[0] - o_mp.amp(p, mid)[0]) > 1e-6
+
+
+def test_reim_reproduces_complex_linear_function():
+    """No resonances and knot values alpha + beta s_k (complex alpha, beta): the
+    natural spline of each part is that line exactly, in every segment and
+    beyond the end knots, so A = 2 alpha + beta (s12 + s13)."""
+    knots = synth.uniform_knots(0.3, 2.6, 9)  # end knots inside the plot's range
+    spec = synth.ModelSpec(name="lin", mD=synth.M_D, m1=synth.M_PI, m2=synth.M_PI,
+                           resonances=(), knots=knots, swave_form="reim")
+    o = oracle.Oracle(spec)
+    alpha, beta = 0.7 - 0.2j, -0.35 + 1.1j
+    z = alpha + beta * np.asarray(knots)
+    pts = spec.s_lo + (spec.s_hi - spec.s_lo) * RNG.random((3000, 2))
+    pts = pts[o.inside(pts)]
+    assert (pts[:, 0] < knots[0]).any() and (pts[:, 0] > knots[-1]).any()
+    got = o.amp(np.concatenate([z.real, z.imag]), pts)
+    np.testing.assert_allclose(got, 2 * alpha + beta * (pts[:, 0] + pts[:, 1]), rtol=1e-12,
+                               atol=1e-12)
+
+
+@pytest.mark.parametrize("spec", REIM_SPECS, ids=lambda s: s.name)
+def test_reim_amplitude_is_linear_in_all_parameters(spec):
+    """A = sum_r c_r B_r + sum_k (x_k + i y_k) W_k with W_k the natural-spline
+    cardinal function of knot k summed over both channels (scipy builds it):
+    |A|^2 is then a Hermitian form in the complex parameters and the
+    normalisation integral is theta^H M theta with M the mean of conj(b) b^T."""
+    from scipy.interpolate import CubicSpline
+
+    o = oracle.Oracle(spec)
+    p = synth.perturbed_params(spec, 29)
+    R, N = spec.n_res, spec.n_knots
+    pts = spec.s_lo + (spec.s_hi - spec.s_lo) * RNG.random((4000, 2))
+    pts = pts[o.inside(pts)]
+    k = np.asarray(spec.knots)
+    W = np.zeros((len(pts), N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        cs = CubicSpline(k, e, bc_type="natural", extrapolate=True)
+        W[:, j] = cs(pts[:, 0]) + cs(pts[:, 1])
+    b = np.concatenate([o.basis(pts), W.astype(complex)], axis=1)
+    theta = np.concatenate([p[0:2 * R:2] + 1j * p[1:2 * R:2],
+                            p[2 * R:2 * R + N] + 1j * p[2 * R + N:]])
+    np.testing.assert_allclose(o.amp(p, pts), b @ theta, rtol=1e-10, atol=1e-12)
+    M = (b.conj().T @ b) / len(pts)
+    I_form = (theta.conj() @ M @ theta).real
+    assert I_form == pytest.approx(np.mean(o.amp2(p, pts)), rel=1e-11)
+
+
+@pytest.mark.parametrize("spec", REIM_SPECS, ids=lambda s: s.name)
+def test_reim_nll_invariant_under_complex_scaling(spec):
+    """A is linear in (c, x + i y): theta -> lambda theta scales A by lambda for
+    any complex lambda, which leaves -2 ln L unchanged; the gradient is
+    orthogonal to both the scale and the rotation direction."""
+    o, data, norm = _small_problem(spec)
+    p = synth.perturbed_params(spec, 31, 0.02)
+    R, N = spec.n_res, spec.n_knots
+    v0, g = o.nll_grad(p, data, norm)
+    th = np.concatenate([p[0:2 * R:2] + 1j * p[1:2 * R:2], p[2 * R:2 * R + N] + 1j * p[2 * R + N:]])
+
+    def to_params(t):
+        q = np.empty_like(p)
+        q[0:2 * R:2], q[1:2 * R:2] = t[:R].real, t[:R].imag
+        q[2 * R:2 * R + N], q[2 * R + N:] = t[R:].real, t[R:].imag
+        return q
+
+    lam = 1.3 * np.exp(0.77j)
+    assert o.nll(to_params(lam * th), data, norm) == pytest.approx(v0, rel=1e-12, abs=1e-9)
+    gn = np.linalg.norm(g)
+    for d in (to_params(th), to_params(1j * th)):
+        assert abs(g @ d) < 1e-9 * gn * np.linalg.norm(d)
+
+
+@pytest.mark.parametrize("spec", REIM_SPECS, ids=lambda s: s.name)
+def test_reim_gradient_central_differences(spec):
+    o, data, norm = _small_problem(spec)
+    p = synth.perturbed_params(spec, 37, 0.02)
+    _, g = o.nll_grad(p, data, norm)
+    h = 1e-6
+    fd = np.empty_like(p)
+    for k in range(len(p)):
+        e = np.zeros_like(p)
+        e[k] = h
+        fd[k] = (o.nll(p + e, data, norm) - o.nll(p - e, data, norm)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-5 * np.abs(g).max())
