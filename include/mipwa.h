@@ -28,6 +28,8 @@
  *
  * Parameter vector (P = 2R + 2N doubles, R resonances, N knots):
  *   [Re c_0, Im c_0, ..., Re c_{R-1}, Im c_{R-1}, a_0..a_{N-1}, phi_0..phi_{N-1}]
+ * (with the S-wave form MIPWA_SWAVE_REIM the knot block is [x_0..x_{N-1},
+ * y_0..y_{N-1}], the real and imaginary parts of the knot values).
  *
  * Event layout: n interleaved pairs (s12, s13), either double (MIPWA_F64) or
  * float (MIPWA_F32), in GeV^2.
@@ -128,6 +130,40 @@ int mipwa_set_events(mipwa_ctx* ctx, const void* s12s13, int64_t n, int dtype,
  * phase-space sample), same conventions as mipwa_set_events; n >= 1. */
 int mipwa_set_norm_sample(mipwa_ctx* ctx, const void* s12s13, int64_t n, int dtype,
                           int on_device, int64_t* n_outside);
+
+/* S-wave knot parametrisation (Sec. 2: the S-wave is a cubic spline "in the
+ * complex plane" through complex values at the N boundary points).
+ *   MIPWA_SWAVE_MAGPHASE (default): knot block [a_k..., phi_k...],
+ *     A0(s) = a(s) exp(i phi(s)), magnitude and phase splined separately.
+ *   MIPWA_SWAVE_REIM: knot block [x_k..., y_k...], A0(s) = x(s) + i y(s),
+ *     real and imaginary parts splined separately; A is then linear in every
+ *     parameter (c_r and x_k + i y_k).
+ * Same natural splines, knots and end-segment continuation in both forms.
+ * Stored events and the basis cache stay valid. Returns MIPWA_EINVAL for any
+ * other value. */
+#define MIPWA_SWAVE_MAGPHASE 0
+#define MIPWA_SWAVE_REIM 1
+int mipwa_set_swave_form(mipwa_ctx* ctx, int form);
+
+/* Normalisation from per-cell moments (form MIPWA_SWAVE_REIM only; on != 0
+ * switches it on, 0 off). With A linear in the parameters, sum_j |A(y_j)|^2
+ * over the normalisation sample is a Hermitian form in them (Sec. 2: the
+ * integral of |A|^2 over the Dalitz plot, taken as the sample mean). Within
+ * one spline cell (j12, j13) each event's amplitude is b^T theta_cell with
+ * the local basis b = (B_0..B_{R-1}, 1, t12, t12^2, t12^3, t13, t13^2,
+ * t13^3), B_r the Bose-symmetrised Breit-Wigner terms and t = s - s_j, so the
+ * context stores once, in FP64, the cell sums of conj(b) b^T: 22 + 14R + R^2
+ * doubles per cell ((N-1)^2 cells). Every evaluation then takes the integral
+ * and its gradient from these moments and the current spline cubics, with
+ * O(cells) work instead of O(N_norm) events; the value equals the direct sum
+ * up to rounding. The moments are rebuilt on the first evaluation after
+ * set_masses, set_model or set_norm_sample; mipwa_build_norm_gram builds them
+ * at once (to time that cost apart). Evaluations return MIPWA_ESTATE while
+ * the form is MIPWA_SWAVE_MAGPHASE, and MIPWA_EINVAL when the normalisation
+ * sample holds 2^31 events or more. Batched toys (mipwa_nll_grad_toys) use
+ * the moments too. */
+int mipwa_enable_norm_gram(mipwa_ctx* ctx, int on);
+int mipwa_build_norm_gram(mipwa_ctx* ctx);
 
 /* Cached per-event basis (on != 0): with the Breit-Wigner masses, widths and
  * radii fixed, the Bose-symmetrised terms A_r(s12,s13) + A_r(s13,s12) of Eq. 1

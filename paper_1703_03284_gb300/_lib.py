@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libmipwa.so")
 
 OK, EINVAL, EOUTSIDE, ENONPOS, ECUDA, ETIMEOUT, ESTATE, ENOMEM = 0, -1, -2, -3, -4, -5, -6, -7
 F64, F32 = 0, 1
+SWAVE_MAGPHASE, SWAVE_REIM = 0, 1
 MAX_RES = 4
 MAX_KNOTS = 64
 MAX_TOYS = 4096
@@ -40,6 +41,9 @@ SIGNATURES = [
     ("mipwa_set_events", _i, [_vp, _vp, _i64, _i, _i, _pi64]),
     ("mipwa_set_norm_sample", _i, [_vp, _vp, _i64, _i, _i, _pi64]),
     ("mipwa_enable_basis_cache", _i, [_vp, _i]),
+    ("mipwa_set_swave_form", _i, [_vp, _i]),
+    ("mipwa_enable_norm_gram", _i, [_vp, _i]),
+    ("mipwa_build_norm_gram", _i, [_vp]),
     ("mipwa_num_params", _i, [_vp]),
     ("mipwa_nll", _i, [_vp, _pd, _pd]),
     ("mipwa_nll_grad", _i, [_vp, _pd, _pd, _pd]),

@@ -114,10 +114,27 @@ class Likelihood:
         self.n_params = self.num_params()
 
     def set_spec(self, spec):
-        """set_masses + set_model from an object with mD, m1, m2, resonances,
-        knots, r_res, r_D attributes."""
+        """set_masses + set_model (+ set_swave_form) from an object with mD, m1,
+        m2, resonances, knots, r_res, r_D (and optionally swave_form)
+        attributes."""
         self.set_masses(spec.mD, spec.m1, spec.m2)
         self.set_model(spec.resonances, spec.knots, spec.r_res, spec.r_D)
+        self.set_swave_form(getattr(spec, "swave_form", "magphase"))
+
+    def set_swave_form(self, form):
+        """"magphase" (knot block [a_k, phi_k]) or "reim" (knot block [x_k, y_k],
+        A0 = x(s) + i y(s)); or the MIPWA_SWAVE_* code."""
+        code = {"magphase": _lib.SWAVE_MAGPHASE, "reim": _lib.SWAVE_REIM}.get(form, form)
+        self._check(self._lib.mipwa_set_swave_form(self._h, int(code)))
+
+    def enable_norm_gram(self, on: bool = True):
+        """Normalisation from per-cell moments of the normalisation sample
+        (Re/Im form only)."""
+        self._check(self._lib.mipwa_enable_norm_gram(self._h, int(bool(on))))
+
+    def build_norm_gram(self):
+        self._follow_stream()
+        self._check(self._lib.mipwa_build_norm_gram(self._h))
 
     def _set(self, fn, x):
         self._follow_stream()

@@ -55,6 +55,13 @@ struct mipwa_ctx {
     bool no_sort = false;   // keep the caller's order (toy ranges)
   } data, norm, toys;
   bool basis_on = false;
+  // Re/Im form: normalisation from per-cell moments of the normalisation sample
+  bool gram_on = false;
+  bool gram_valid = false;
+  int* d_cells = nullptr;      // first[nkeys] | last[nkeys]
+  size_t cells_cap = 0;        // bytes
+  double* d_gram = nullptr;    // nkeys * gram_moments(R)
+  size_t gram_cap = 0;         // bytes
   // batched toys
   struct Toys {
     int n = 0;
@@ -275,6 +282,36 @@ void invalidate_basis(mipwa_ctx* c) {
   invalidate_graph(c);
 }
 
+// Per-cell moments of the normalisation sample for the current model (Re/Im
+// form): cell ranges of the grouped sample, then one block per cell.
+int build_gram(mipwa_ctx* c) {
+  if (c->gram_valid) return MIPWA_OK;
+  auto& smp = c->norm;
+  if (!(smp.sorted || smp.n == 1))
+    return fail(c, MIPWA_EINVAL, "the moment normalisation needs a sample of fewer than 2^31 events");
+  const int nseg = c->model.kn.n - 1, nkeys = nseg * nseg;
+  const int M = gram_moments(c->model.n_res);
+  int rc = ensure(c, (void**)&c->d_cells, &c->cells_cap, 2 * (size_t)nkeys * sizeof(int));
+  if (!rc) rc = ensure(c, (void**)&c->d_gram, &c->gram_cap, (size_t)nkeys * M * sizeof(double));
+  if (rc) return rc;
+  const int ev32 = smp.dtype == MIPWA_F32;
+  CK(c, launch_cell_bounds(ev32, c->model.kn, smp.cur, smp.n, c->d_cells, c->d_cells + nkeys,
+                           grid_for(c, smp.n), c->stream));
+  CK(c, launch_gram_build(ev32, c->model, smp.cur, c->d_cells, c->d_cells + nkeys, c->d_gram,
+                          c->stream));
+  c->launches += 2;
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->gram_valid = true;
+  return MIPWA_OK;
+}
+
+// Evaluations with the moment normalisation need the Re/Im form.
+int gram_state(mipwa_ctx* c) {
+  if (c->gram_on && !c->model.reim)
+    return fail(c, MIPWA_ESTATE, "the moment normalisation needs the Re/Im S-wave form");
+  return MIPWA_OK;
+}
+
 // (Re)build the cached Breit-Wigner basis of a sample for the current model
 // and compute mode.
 int build_basis(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
@@ -371,36 +408,56 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   if (!c->norm.set) return fail(c, MIPWA_ESTATE, "set_norm_sample must come first");
   if (c->data.n > 0 && c->data.dtype != c->norm.dtype)
     return fail(c, MIPWA_EINVAL, "data and normalisation samples must share a dtype");
+  rc = gram_state(c);
+  if (rc) return rc;
   const int P = c->n_params;
   for (int k = 0; k < P; ++k)
     if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
   const int f32 = c->mode == MIPWA_F32;
   const int ev32 = c->norm.dtype == MIPWA_F32;
+  const bool gram = c->gram_on;
+  const int nseg = c->model.kn.n - 1;
   // one block count for nll and nll_grad, so they sum identically
   const int per_sm = eval_blocks_per_sm(f32, ev32, c->model, c->basis_on);
   int total = c->sm_count * per_sm;
   const int64_t need_d = (c->data.n + kThreads - 1) / kThreads;
   const int64_t need_n = (c->norm.n + kThreads - 1) / kThreads;
-  int nb_d = 0;
-  if (c->data.n > 0) {
-    const double frac = (double)c->data.n / (double)(c->data.n + c->norm.n);
-    nb_d = (int)std::lround(total * frac);
-    if (nb_d < 1) nb_d = 1;
-    if (nb_d > total - 1) nb_d = total - 1;
-    if (nb_d > need_d) nb_d = (int)need_d;
+  int nb_d = 0, nb_n = 0, grid = 0, rows = 0;
+  if (gram) {
+    // the event kernel runs over the data only; N-1 moment rows stand in for
+    // the normalisation blocks
+    nb_d = (int)std::min<int64_t>(total, std::max<int64_t>(need_d, 1));
+    nb_n = nseg;
+    grid = nb_d;
+    rows = nb_d + nseg;
+  } else {
+    if (c->data.n > 0) {
+      const double frac = (double)c->data.n / (double)(c->data.n + c->norm.n);
+      nb_d = (int)std::lround(total * frac);
+      if (nb_d < 1) nb_d = 1;
+      if (nb_d > total - 1) nb_d = total - 1;
+      if (nb_d > need_d) nb_d = (int)need_d;
+    }
+    nb_n = total - nb_d;
+    if (nb_n > need_n) nb_n = (int)need_n;
+    if (nb_n < 1) nb_n = 1;
+    grid = nb_d + nb_n;
+    rows = grid;
   }
-  int nb_n = total - nb_d;
-  if (nb_n > need_n) nb_n = (int)need_n;
-  if (nb_n < 1) nb_n = 1;
-  const int grid = nb_d + nb_n;
   const int W = partial_width(c->model.kn.n, c->model.n_res, want_grad);
-  rc = ensure(c, (void**)&c->d_partials, &c->partials_cap, (size_t)grid * W * sizeof(double));
+  rc = ensure(c, (void**)&c->d_partials, &c->partials_cap, (size_t)rows * W * sizeof(double));
   if (rc) return rc;
 
   if (c->basis_on) {
     rc = build_basis(c, c->data);
     if (rc) return rc;
-    rc = build_basis(c, c->norm);
+    if (!gram) {
+      rc = build_basis(c, c->norm);
+      if (rc) return rc;
+    }
+  }
+  if (gram) {
+    rc = build_gram(c);
     if (rc) return rc;
   }
   std::memcpy(c->h_stage, params, P * sizeof(double));
@@ -425,9 +482,14 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   a.out = c->d_out;
   a.flags = c->d_flags;
   a.basis_data = c->basis_on ? c->data.basis : nullptr;
-  a.basis_norm = c->basis_on ? c->norm.basis : nullptr;
+  a.basis_norm = (c->basis_on && !gram) ? c->norm.basis : nullptr;
   a.model = c->model;
   if (c->timing) CK(c, cudaEventRecord(c->ev0, c->stream));
+  if (gram) {
+    CK(c, launch_gram_rows(want_grad, f32, c->model, c->d_coef, 0, c->d_gram,
+                           c->d_partials + (size_t)nb_d * W, nseg, 1, c->stream));
+    c->launches++;
+  }
   CK(c, launch_eval(f32, ev32, want_grad, a, grid, c->stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, c->stream));
   c->launches += 2;
@@ -459,7 +521,10 @@ int plan_toys(mipwa_ctx* c) {
   auto& q = c->tq;
   const int T = q.n;
   const int64_t nn = c->norm.n;
-  const int C = (int)((nn + q.norm_chunk - 1) / q.norm_chunk);
+  // with the moment normalisation the first N-1 rows of each toy are the
+  // moment rows and there are no normalisation items
+  const bool gram = c->gram_on;
+  const int C = gram ? c->model.kn.n - 1 : (int)((nn + q.norm_chunk - 1) / q.norm_chunk);
   std::vector<int> drows(T);
   int dmax = 0;
   for (int t = 0; t < T; ++t) {
@@ -470,7 +535,7 @@ int plan_toys(mipwa_ctx* c) {
   const int rpt = C + dmax;
   std::vector<ToyItem> items;
   items.reserve((size_t)T * C + (size_t)T * dmax);
-  for (int ch = 0; ch < C; ++ch)
+  for (int ch = 0; ch < (gram ? 0 : C); ++ch)
     for (int t = 0; t < T; ++t)
       items.push_back(ToyItem{t, 0, (int64_t)ch * q.norm_chunk,
                               std::min(nn, (int64_t)(ch + 1) * q.norm_chunk), t * rpt + ch});
@@ -511,6 +576,9 @@ int enqueue_toys(mipwa_ctx* c, cudaStream_t st) {
   CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), st));
   launch_prepare(c->model, q.d_params, c->d_lu, q.d_coef, q.d_coef32, st, T);
   CK(c, cudaGetLastError());
+  if (c->gram_on)
+    CK(c, launch_gram_rows(true, f32, c->model, q.d_coef, coef_size(c->model.kn.n, c->model.n_res),
+                           c->d_gram, q.d_partials, q.rows_per_toy, T, st));
   ToyArgs a;
   a.data = c->toys.cur;
   a.norm = c->norm.cur;
@@ -531,7 +599,7 @@ int enqueue_toys(mipwa_ctx* c, cudaStream_t st) {
   a.out = q.d_out;
   a.flags = c->d_flags;
   a.basis_data = c->basis_on ? c->toys.basis : nullptr;
-  a.basis_norm = c->basis_on ? c->norm.basis : nullptr;
+  a.basis_norm = (c->basis_on && !c->gram_on) ? c->norm.basis : nullptr;
   a.model = c->model;
   CK(c, launch_toys(f32, ev32, a, q.grid, st));
   CK(c, cudaMemcpyAsync(q.h_out, q.d_out, (size_t)T * (1 + P) * sizeof(double),
@@ -550,10 +618,15 @@ int run_toys(mipwa_ctx* c) {
   if (!c->toys.set || q.n == 0) return fail(c, MIPWA_ESTATE, "set_toys must come first");
   if (c->toys.n > 0 && c->toys.dtype != c->norm.dtype)
     return fail(c, MIPWA_EINVAL, "toy and normalisation samples must share a dtype");
-  int rc;
+  int rc = gram_state(c);
+  if (rc) return rc;
   if (c->basis_on) {
     rc = build_basis(c, c->toys);
-    if (!rc) rc = build_basis(c, c->norm);
+    if (!rc && !c->gram_on) rc = build_basis(c, c->norm);
+    if (rc) return rc;
+  }
+  if (c->gram_on) {
+    rc = build_gram(c);
     if (rc) return rc;
   }
   if (!q.planned) {
@@ -578,11 +651,11 @@ int run_toys(mipwa_ctx* c) {
       CK(c, cudaGraphInstantiate(&q.exec, q.graph, 0));
     }
     CK(c, cudaGraphLaunch(q.exec, c->stream));
-    c->launches += 3;
+    c->launches += c->gram_on ? 4 : 3;
   } else {
     rc = enqueue_toys(c, c->stream);
     if (rc) return rc;
-    c->launches += 3;
+    c->launches += c->gram_on ? 4 : 3;
   }
   CK(c, cudaStreamSynchronize(c->stream));
   return MIPWA_OK;
@@ -640,6 +713,7 @@ void mipwa_destroy(mipwa_ctx* c) {
                   (void*)c->d_out,
                   (void*)c->d_flags, (void*)c->d_counter, (void*)c->d_count,
                   (void*)c->d_partials, (void*)c->d_sortwork, c->data.basis, c->norm.basis,
+                  (void*)c->d_cells, (void*)c->d_gram,
                   c->data.cur, c->data.spare, c->norm.cur,
                   c->norm.spare})
     if (p) cudaFree(p);
@@ -689,6 +763,7 @@ int mipwa_set_masses(mipwa_ctx* c, double mD, double m1, double m2) {
   derive(c->model, nullptr, 0, 0.0, 0.0);
   c->have_masses = true;
   c->have_model = false;
+  c->gram_valid = false;
   invalidate_basis(c);
   c->n_params = -1;
   c->data.set = c->norm.set = false;
@@ -743,6 +818,7 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   c->n_params = 2 * n_res + 2 * n_knots;
   c->have_model = true;
   c->tq.planned = false;
+  c->gram_valid = false;
   invalidate_basis(c);
   rc = resort(c, c->data);
   if (rc) return rc;
@@ -761,9 +837,41 @@ int mipwa_set_norm_sample(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, i
   const int rc = set_sample(c, c->norm, ptr, n, dtype, on_device, n_outside, false);
   if (rc == MIPWA_OK) {
     c->tq.planned = false;
+    c->gram_valid = false;
     invalidate_graph(c);
   }
   return rc;
+}
+
+int mipwa_set_swave_form(mipwa_ctx* c, int form) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (form != MIPWA_SWAVE_MAGPHASE && form != MIPWA_SWAVE_REIM)
+    return fail(c, MIPWA_EINVAL, "unknown S-wave form %d", form);
+  c->model.reim = form == MIPWA_SWAVE_REIM;
+  c->tq.planned = false;  // the toys' work list depends on the normalisation method
+  invalidate_graph(c);
+  return MIPWA_OK;
+}
+
+int mipwa_enable_norm_gram(mipwa_ctx* c, int on) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->gram_on = on != 0;
+  c->tq.planned = false;
+  invalidate_graph(c);
+  return MIPWA_OK;
+}
+
+int mipwa_build_norm_gram(mipwa_ctx* c) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  if (!c->norm.set) return fail(c, MIPWA_ESTATE, "set_norm_sample must come first");
+  if (!c->gram_on) return fail(c, MIPWA_ESTATE, "enable_norm_gram must come first");
+  rc = gram_state(c);
+  if (rc) return rc;
+  return build_gram(c);
 }
 
 int mipwa_num_params(const mipwa_ctx* c) { return (c && c->have_model) ? c->n_params : -1; }

@@ -125,26 +125,6 @@ struct SwavePart {
 };
 
 // ---------------------------------------------------------------- FP64 form
-// Bose-symmetrised Breit-Wigner basis B_r = A_r(s12,s13) + A_r(s13,s12).
-__device__ __forceinline__ void bw_basis(const Model& m, double s12, double s13,
-                                         Cplx<double>* B) {
-  const ConstsD& c = m.cd;
-  const ChanD k12 = channel_d(c, s12);
-  const ChanD k13 = channel_d(c, s13);
-  double z1a, z2a, z1b, z2b;
-  zemach_d(c, k12, s13, z1a, z2a);
-  zemach_d(c, k13, s12, z1b, z2b);
-#pragma unroll
-  for (int r = 0; r < kMaxRes; ++r) {
-    if (r < m.n_res) {
-      const Cplx<double> u = bw_d(c, r, k12, z1a, z2a);
-      const Cplx<double> v = bw_d(c, r, k13, z1b, z2b);
-      B[r].re = u.re + v.re;
-      B[r].im = u.im + v.im;
-    }
-  }
-}
-
 // A = sum_r c_r B_r
 template <int NR>
 __device__ __forceinline__ Cplx<double> combine(const Model& m, const EvalSmem<double>& sm,
@@ -160,14 +140,19 @@ __device__ __forceinline__ Cplx<double> combine(const Model& m, const EvalSmem<d
   return A;
 }
 
-// A += a(s) e^{i phi(s)} for one channel.
+// A += a(s) e^{i phi(s)} for one channel (Re/Im form: A += x(s) + i y(s)).
 __device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<double>& sm, double s,
-                                          SwavePart<double>& w, Cplx<double>& A) {
+                                          bool reim, SwavePart<double>& w, Cplx<double>& A) {
   w.j = segment_of(m.kn, sm.knot, s);
   w.t = s - sm.knot[w.j];
   const double* a = &sm.coef[w.j * 8];
   w.a = ((a[3] * w.t + a[2]) * w.t + a[1]) * w.t + a[0];
   const double ph = ((a[7] * w.t + a[6]) * w.t + a[5]) * w.t + a[4];
+  if (reim) {
+    A.re += w.a;
+    A.im += ph;
+    return;
+  }
   sincos(ph, &w.sn, &w.cs);
   A.re += w.a * w.cs;
   A.im += w.a * w.sn;
@@ -223,12 +208,17 @@ __device__ __forceinline__ Cplx<float> combine(const Model& m, const EvalSmem<fl
 }
 
 __device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<float>& sm, float s,
-                                          SwavePart<float>& w, Cplx<float>& A) {
+                                          bool reim, SwavePart<float>& w, Cplx<float>& A) {
   w.j = segment_of(m.kn, sm.knot, s);
   w.t = __fsub_rn(s, sm.knot[w.j]);  // exact (Sterbenz) on the knot grids used here
   const float4* c4 = reinterpret_cast<const float4*>(&sm.coef[w.j * 16]);
   const F2 a = cubic_hl(c4[0], c4[1], w.t);
   const F2 ph = cubic_hl(c4[2], c4[3], w.t);
+  if (reim) {
+    A.re += a.hi + a.lo;
+    A.im += ph.hi + ph.lo;
+    return;
+  }
   sincos_cw(ph.hi, ph.lo, &w.sn, &w.cs);
   w.a = a.hi;
   A.re += mul_hl(a.hi, a.lo, w.cs);
@@ -254,8 +244,9 @@ __device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& 
     bw_basis(m, s12, s13, B);
   }
   Cplx<T> A = combine<NR>(m, sm, B);
-  swave_add(m, sm, s12, w12, A);
-  swave_add(m, sm, s13, w13, A);
+  const bool reim = SIG == 0 && m.reim;  // the specialised kernels serve magnitude/phase only
+  swave_add(m, sm, s12, reim, w12, A);
+  swave_add(m, sm, s13, reim, w13, A);
   return A;
 }
 
@@ -270,13 +261,14 @@ __device__ __forceinline__ void bin_add(EvalSmem<T>& sm, int idx, T v) {
 
 // Adjoint of one channel's S-wave, as the 8 contributions to its segment's
 // polynomial bins: d|A|^2/d a(s) = 2 Re(A* e^{i phi}) and
-// d|A|^2/d phi(s) = 2 a Re(A* i e^{i phi}), times t^m, t = s - s_j (the exact
-// knot: the FP32 form evaluates about float(s_j) and shifts back here).
+// d|A|^2/d phi(s) = 2 a Re(A* i e^{i phi}) (Re/Im form: d|A|^2/dx(s) = 2 Re A,
+// d|A|^2/dy(s) = 2 Im A), times t^m, t = s - s_j (the exact knot: the FP32
+// form evaluates about float(s_j) and shifts back here).
 template <typename T>
 __device__ __forceinline__ void swave_adjoint(const EvalSmem<T>& sm, const SwavePart<T>& w,
-                                              Cplx<T> A, T wt, T* v) {
-  const T abar = T(2) * wt * (A.re * w.cs + A.im * w.sn);
-  const T pbar = T(2) * wt * w.a * (A.im * w.cs - A.re * w.sn);
+                                              bool reim, Cplx<T> A, T wt, T* v) {
+  const T abar = reim ? T(2) * wt * A.re : T(2) * wt * (A.re * w.cs + A.im * w.sn);
+  const T pbar = reim ? T(2) * wt * A.im : T(2) * wt * w.a * (A.im * w.cs - A.re * w.sn);
   T t1 = w.t;
   if constexpr (std::is_same<T, float>::value) t1 = w.t - sm.knot_lo[w.j];
   const T t2 = t1 * t1, t3 = t2 * t1;
@@ -529,8 +521,9 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
             gc[2 * r + 1] += T(2) * wt * (A.im * B[r].re - A.re * B[r].im);
           }
         }
-        swave_adjoint(sm, w12, A, wt, v);
-        swave_adjoint(sm, w13, A, wt, v + 8);
+        const bool reim = SIG == 0 && m.reim;
+        swave_adjoint(sm, w12, reim, A, wt, v);
+        swave_adjoint(sm, w13, reim, A, wt, v + 8);
       } else {
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = T(0);
@@ -742,9 +735,10 @@ static cudaError_t run_eval(const EvalArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// The model's compile-time signature, if a specialised FP32 kernel exists.
+// The model's compile-time signature, if a specialised FP32 kernel exists
+// (magnitude/phase S-wave only).
 static int model_sig(const Model& m) {
-  if (m.n_res == 2 && m.cf.L[0] == 1 && m.cf.L[1] == 2) return kSigPD;
+  if (!m.reim && m.n_res == 2 && m.cf.L[0] == 1 && m.cf.L[1] == 2) return kSigPD;
   return 0;
 }
 
@@ -762,7 +756,7 @@ static cudaError_t dispatch_eval(bool grad, bool cached, bool pd, const EvalArgs
 
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t st) {
-  const bool cached = a.basis_norm != nullptr;
+  const bool cached = a.basis_norm != nullptr || a.basis_data != nullptr;
   const bool pd = model_sig(a.model) == kSigPD;
   if (compute_f32) {
     if (ev_f32) return dispatch_eval<float, float2>(grad, cached, pd, a, grid, st);
@@ -784,7 +778,7 @@ static cudaError_t run_toys(bool cached, const ToyArgs& a, int grid, cudaStream_
 
 cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int grid,
                         cudaStream_t st) {
-  const bool cached = a.basis_norm != nullptr;
+  const bool cached = a.basis_norm != nullptr || a.basis_data != nullptr;
   if (compute_f32) return ev_f32 ? run_toys<float, float2>(cached, a, grid, st)
                                  : run_toys<float, double2>(cached, a, grid, st);
   return ev_f32 ? run_toys<double, float2>(cached, a, grid, st)

@@ -89,5 +89,22 @@ int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached)
 cudaError_t sort_workspace_ints(int n_knots, size_t* ints);
 cudaError_t launch_sort(int ev_f32, const Knots& kn, const void* src, int64_t n, void* dst,
                         int* work, cudaStream_t stream);
+// Index range [first[k], last[k]) of every spline cell k = j12 (N-1) + j13 in
+// a sample grouped by cell (n < 2^31); empty cells get [0, 0).
+cudaError_t launch_cell_bounds(int ev_f32, const Knots& kn, const void* ev, int64_t n, int* first,
+                               int* last, int grid, cudaStream_t stream);
+
+// Re/Im form: per-cell moments (gram_moments(R) doubles per cell, (N-1)^2
+// cells) of a sample grouped by cell, FP64.
+cudaError_t launch_gram_build(int ev_f32, const Model& m, const void* ev, const int* first,
+                              const int* last, double* moments, cudaStream_t stream);
+// Re/Im form: the normalisation rows of n_sets parameter sets (coefficients
+// at coef + set * coef_stride, prepare-kernel layout): set s writes rows
+// [s * row_stride, s * row_stride + N - 1) of `rows` in the partial-row layout
+// (partial_width(N, R, grad) doubles each). FP32 compute mode: the c_r
+// columns are in units of B_r / cscale_r, as the FP32 event kernels write them.
+cudaError_t launch_gram_rows(bool grad, int compute_f32, const Model& m, const double* coef,
+                             int coef_stride, const double* moments, double* rows,
+                             int row_stride, int n_sets, cudaStream_t stream);
 
 }  // namespace mipwa

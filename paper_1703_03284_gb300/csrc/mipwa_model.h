@@ -69,6 +69,7 @@ struct Knots {
 
 struct Model {
   int n_res;
+  int reim;  // S-wave knots are (Re, Im) of the knot values, not (magnitude, phase)
   double mD, m1, m2;
   ConstsD cd;
   ConstsF cf;
@@ -88,7 +89,8 @@ struct SplineLU {
 
 // Per-segment polynomial coefficients written by the prepare kernel:
 // coef[j*8 + 0..3] = magnitude a(s) = sum_m alpha_m t^m, t = s - s_j,
-// coef[j*8 + 4..7] = phase phi(s)   = sum_m beta_m t^m;
+// coef[j*8 + 4..7] = phase phi(s)   = sum_m beta_m t^m
+// (Re/Im form: the real part x(s) and the imaginary part y(s));
 // followed by 2R doubles (Re c_r, Im c_r).
 MIPWA_HD inline int coef_size(int n_knots, int n_res) { return 8 * (n_knots - 1) + 2 * n_res; }
 
@@ -106,5 +108,19 @@ MIPWA_HD inline int coef32_size(int n_knots, int n_res) {
 MIPWA_HD inline int partial_width(int n_knots, int n_res, bool grad) {
   return grad ? 1 + 2 * n_res + 8 * (n_knots - 1) : 1;
 }
+
+// Per-cell moments of the normalisation sample (Re/Im form), for a cell
+// (j12, j13) with t1 = s12 - s_j12, t2 = s13 - s_j13 and the Bose-symmetrised
+// Breit-Wigner terms B_r, all summed over the cell's events:
+//   [0..6]    sum t1^k, k = 0..6 (k = 0: the event count)
+//   [7..12]   sum t2^k, k = 1..6
+//   [13..21]  sum t1^a t2^b, a, b = 1..3 (index 13 + 3(a-1) + (b-1))
+//   [22 + 14r + 0..3]   sum Re B_r t1^a, a = 0..3
+//   [22 + 14r + 4..7]   sum Im B_r t1^a, a = 0..3
+//   [22 + 14r + 8..10]  sum Re B_r t2^b, b = 1..3
+//   [22 + 14r + 11..13] sum Im B_r t2^b, b = 1..3
+//   [22 + 14R + r]      sum |B_r|^2
+//   then for r < s in lexicographic order: sum Re(conj(B_r) B_s), sum Im(conj(B_r) B_s)
+MIPWA_HD inline int gram_moments(int n_res) { return 22 + 14 * n_res + n_res * n_res; }
 
 }  // namespace mipwa

@@ -172,6 +172,32 @@ __global__ void __launch_bounds__(32) sort_scatter_kernel(const Knots kn, const 
   }
 }
 
+// first[k], last[k] = the index range of key k in a sample grouped by key
+// (both zeroed beforehand: an empty key keeps 0, 0).
+template <typename EvT>
+__global__ void __launch_bounds__(256) cell_bounds_kernel(const Knots kn, const EvT* ev, int64_t n,
+                                                          int* first, int* last) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = key_of(kn, ev[i]);
+    if (i == 0 || key_of(kn, ev[i - 1]) != k) first[k] = (int)i;
+    if (i == n - 1 || key_of(kn, ev[i + 1]) != k) last[k] = (int)(i + 1);
+  }
+}
+
+cudaError_t launch_cell_bounds(int ev_f32, const Knots& kn, const void* ev, int64_t n, int* first,
+                               int* last, int grid, cudaStream_t st) {
+  const int nkeys = (kn.n - 1) * (kn.n - 1);
+  cudaError_t e = cudaMemsetAsync(first, 0, nkeys * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(last, 0, nkeys * sizeof(int), st);
+  if (e != cudaSuccess || n == 0) return e;
+  if (ev_f32)
+    cell_bounds_kernel<float2><<<grid, 256, 0, st>>>(kn, (const float2*)ev, n, first, last);
+  else
+    cell_bounds_kernel<double2><<<grid, 256, 0, st>>>(kn, (const double2*)ev, n, first, last);
+  return cudaGetLastError();
+}
+
 cudaError_t sort_workspace_ints(int n_knots, size_t* ints) {
   const int nkeys = (n_knots - 1) * (n_knots - 1);
   // counts [kSortBlocks][nkeys], group sums [kGroups][nkeys], key starts [nkeys]
