@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cached-steps", type=int, default=10)
     ap.add_argument("--toys-steps", type=int, default=3)
+    ap.add_argument("--reim-steps", type=int, default=10)
     ap.add_argument("--n-toys", type=int, default=256)
     ap.add_argument("--toys-norm", type=int, default=10_000_000)
     ap.add_argument("--paper-fit", type=int, default=1,
@@ -299,6 +300,7 @@ def toys_leg(args, stream, rank):
     e1.record(stream)
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1) / args.toys_steps
+    launches_it = (lik.launch_count() - launches0) / args.toys_steps
     pairs = int(offsets[-1]) + args.n_toys * args.toys_norm
     # looping single-toy evaluations (a few toys timed, scaled to all toys by events)
     loop = {}
@@ -320,15 +322,93 @@ def toys_leg(args, stream, rank):
             ev_done += int(sizes[t]) + args.toys_norm
         loop[name] = {"toys_per_s": 1e3 * 4 / t_done, "event_pairs_per_s": ev_done / (t_done / 1e3),
                       "note": "4 toys timed one by one, same events"}
+    # the same toys with the Re/Im form and the moment normalisation
+    lik.set_swave_form("reim")
+    lik.enable_norm_gram(True)
+    qr = np.stack([to_reim(spec, p) for p in params])
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    lik.build_norm_gram()
+    b1.record(stream)
+    lik.nll_grad_toys(qr)
+    torch.cuda.synchronize()
+    build_ms = b0.elapsed_time(b1)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(args.toys_steps):
+        lik.nll_grad_toys(qr)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    tr_ms = r0.elapsed_time(r1) / args.toys_steps
+    reim = {"ms_per_iteration": tr_ms, "toys_per_s": 1e3 * args.n_toys / tr_ms,
+            "event_pairs_per_s": pairs / (tr_ms / 1e3), "moments_build_ms": build_ms,
+            "dtype": "f32 (cached basis, CUDA graph); normalisation from FP64 cell moments"}
     return {"n_toys": args.n_toys, "events_in_toys": int(offsets[-1]),
             "norm_events": args.toys_norm, "ms_per_iteration": t_ms,
             "toys_per_s": 1e3 * args.n_toys / t_ms,
             "event_pairs_per_s": pairs / (t_ms / 1e3),
             "autotuned_norm_chunk": best,
-            "gpu_launches_per_iteration": (lik.launch_count() - launches0) / args.toys_steps,
+            "gpu_launches_per_iteration": launches_it,
             "loop_single_toy": loop,
             "speedup_vs_fp64_loop": (1e3 * args.n_toys / t_ms) / loop["fp64"]["toys_per_s"],
-            "dtype": "f32 (cached basis, CUDA graph)"}
+            "dtype": "f32 (cached basis, CUDA graph)",
+            "reim_moments": reim}
+
+
+def to_reim(spec, p):
+    """Magnitude/phase parameters -> the same knot values as (Re, Im)."""
+    import numpy as np
+
+    R, N = spec.n_res, spec.n_knots
+    a, phi = p[2 * R:2 * R + N], p[2 * R + N:]
+    return np.concatenate([p[:2 * R], a * np.cos(phi), a * np.sin(phi)])
+
+
+def reim_leg(args, lik, spec, params, events, stream, world):
+    """The same events and knot values with the S-wave spline in the complex
+    plane taken as Re/Im (A linear in all parameters): FP32-mixed with the
+    normalisation summed event by event, then with the per-cell moments
+    (built once, FP64), FP32 and FP64. events/s counts data + normalisation
+    events per evaluation, as the headline does."""
+    import torch
+
+    from paper_1703_03284_gb300 import F32, F64
+
+    q = to_reim(spec, params)
+
+    def timed(steps):
+        lik.nll_grad(q)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            lik.nll_grad(q)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = max_over_ranks(a.elapsed_time(b), world) / steps
+        return {"ms_per_step": t, "value": world * events / (t / 1e3), "unit": "events/s"}
+
+    lik.set_swave_form("reim")
+    out = {"fp32_direct": timed(args.reim_steps)}
+    lik.enable_norm_gram(True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    lik.build_norm_gram()
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["moments_build_ms"] = a.elapsed_time(b)
+    out["moments_doubles"] = (spec.n_knots - 1) ** 2 * (22 + 14 * spec.n_res + spec.n_res ** 2)
+    out["fp32_moments"] = timed(args.reim_steps)
+    lik.set_compute_mode(F64)
+    out["fp64_moments"] = timed(max(1, args.fp64_steps))
+    lik.set_compute_mode(F32)
+    lik.enable_norm_gram(False)
+    lik.set_swave_form("magphase")
+    out["note"] = ("per-step time of the moment form: the moment rows (O(cells)) plus the "
+                   "event kernel over the data events only")
+    return out
 
 
 # ------------------------------------------------------- the paper's own fit
@@ -513,6 +593,9 @@ def run(args, world, rank, local, stream):
                                "traffic": None,
                                "kernel": "eval_kernel<float,float2,grad,cached>"}}
 
+    # ---- Re/Im S-wave form: direct, and with the per-cell moment normalisation
+    reim = reim_leg(args, lik, spec, params, events, stream, world) if args.reim_steps > 0 else None
+
     # ---- end to end from pinned host buffers through the C ABI
     e2e = None
     if args.e2e_steps > 0:
@@ -561,7 +644,8 @@ def run(args, world, rank, local, stream):
                        "l2": "inputs (1.6 GB) larger than L2 (129 MB); no flush needed",
                        "parallelism": f"replicas x{world} (no collective)"},
             "roofline": roofline, "fp64_plain": fp64, "fp32_cached_basis": cached,
-            "batched_toys": toys, "paper_workload_fit": paper, "e2e": e2e,
+            "batched_toys": toys, "reim_moment_normalisation": reim,
+            "paper_workload_fit": paper, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)
