@@ -118,6 +118,28 @@ int mipwa_set_masses(mipwa_ctx* ctx, double mD, double m1, double m2);
 int mipwa_set_model(mipwa_ctx* ctx, const mipwa_resonance* res, int n_res,
                     const double* knots, int n_knots, double r_res, double r_D);
 
+/* Replace the masses, widths and spins of the model's n_res Breit-Wigner terms
+ * (same count, same validity rules as set_model), keeping the knots, radii
+ * and stored samples: the per-resonance constants (pole momenta, barrier
+ * normalisations, running-width factors) are derived again. For fits with
+ * free resonance parameters (Sec. 2 fixes them; the paper mentions them as
+ * model variants). The cached basis and the normalisation moments are rebuilt
+ * on the next evaluation. */
+int mipwa_set_resonances(mipwa_ctx* ctx, const mipwa_resonance* res, int n_res);
+
+/* NLL, its gradient (P doubles, as mipwa_nll_grad) and its derivatives with
+ * respect to the Breit-Wigner pole masses and widths, grad_bw = [dNLL/dm_0,
+ * dNLL/dGamma_0, ..., dNLL/dm_{R-1}, dNLL/dGamma_{R-1}] (2R host doubles), at
+ * the current resonances. The derivatives of each term A_r are analytic: the
+ * width enters only the running width, dA_r/dGamma_r = A_r T i m_r Gamma(s) /
+ * Gamma_r; the mass enters the propagator, the running width (through m_r^2,
+ * q0 and the barrier normalisation) and both barrier normalisations. Always
+ * evaluated in FP64 with the Breit-Wigner terms computed per event and the
+ * normalisation summed over the events, whatever the compute mode, basis
+ * cache or moment setting. Blocks until done. */
+int mipwa_nll_grad_bw(mipwa_ctx* ctx, const double* params, double* nll, double* grad,
+                      double* grad_bw);
+
 /* Data events x_i: n pairs (s12, s13) of type `dtype` at `s12s13` (a device
  * pointer when on_device != 0). n may be 0. Every event must lie inside the
  * Dalitz plot; otherwise the call stores nothing, writes the number of

@@ -38,6 +38,8 @@ SIGNATURES = [
     ("mipwa_set_compute_mode", _i, [_vp, _i]),
     ("mipwa_set_masses", _i, [_vp, _d, _d, _d]),
     ("mipwa_set_model", _i, [_vp, ctypes.POINTER(Resonance), _i, _pd, _i, _d, _d]),
+    ("mipwa_set_resonances", _i, [_vp, ctypes.POINTER(Resonance), _i]),
+    ("mipwa_nll_grad_bw", _i, [_vp, _pd, _pd, _pd, _pd]),
     ("mipwa_set_events", _i, [_vp, _vp, _i64, _i, _i, _pi64]),
     ("mipwa_set_norm_sample", _i, [_vp, _vp, _i64, _i, _i, _pi64]),
     ("mipwa_enable_basis_cache", _i, [_vp, _i]),

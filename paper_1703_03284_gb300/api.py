@@ -112,6 +112,7 @@ class Likelihood:
             self._h, res, len(resonances), kn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             len(kn), float(r_res), float(r_D)))
         self.n_params = self.num_params()
+        self.n_res = len(resonances)
 
     def set_spec(self, spec):
         """set_masses + set_model (+ set_swave_form) from an object with mD, m1,
@@ -135,6 +136,14 @@ class Likelihood:
     def build_norm_gram(self):
         self._follow_stream()
         self._check(self._lib.mipwa_build_norm_gram(self._h))
+
+    def set_resonances(self, resonances: Sequence):
+        """New (mass, width, spin) for the model's resonances (same count);
+        knots, radii and stored samples are kept."""
+        res = (_lib.Resonance * max(len(resonances), 1))()
+        for i, (mass, width, spin) in enumerate(resonances):
+            res[i] = _lib.Resonance(float(mass), float(width), int(spin))
+        self._check(self._lib.mipwa_set_resonances(self._h, res, len(resonances)))
 
     def _set(self, fn, x):
         self._follow_stream()
@@ -217,6 +226,19 @@ class Likelihood:
             self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(out),
             g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out.value, g
+
+    def nll_grad_bw(self, params):
+        """(NLL, dNLL/dparams, [dNLL/dm_r, dNLL/dGamma_r]_r) in FP64 at the
+        current resonance masses and widths."""
+        self._follow_stream()
+        p = self._params(params)
+        pd = ctypes.POINTER(ctypes.c_double)
+        out = ctypes.c_double()
+        g = np.empty_like(p)
+        gbw = np.empty(2 * self.n_res)
+        self._check(self._lib.mipwa_nll_grad_bw(self._h, p.ctypes.data_as(pd), ctypes.byref(out),
+                                                g.ctypes.data_as(pd), gbw.ctypes.data_as(pd)))
+        return out.value, g, gbw
 
     def amp2(self, params, events):
         """|A|^2 per event (0 outside the Dalitz plot) for a CUDA tensor of events;

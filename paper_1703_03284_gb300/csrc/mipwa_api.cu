@@ -23,6 +23,7 @@ struct mipwa_ctx {
   cudaStream_t stream = nullptr;
   bool have_masses = false, have_model = false;
   Model model{};
+  double r_res = 0.0, r_D = 0.0;  // Blatt-Weisskopf radii of the model
   int n_params = -1;
   std::vector<double> lu_host;
   // device buffers
@@ -170,6 +171,22 @@ void derive(Model& m, const mipwa_resonance* res, int n_res, double r_res, doubl
     d.K[r] = d.g[r] * d.nR[r];
     d.ff[r] = std::sqrt(d.nR[r] * d.nD[r]);
     m.cscale[r] = d.ff[r] / (L == 2 ? 3.0 : 1.0);
+    // d/dm_r of q0^2 = lambda(x, a^2, b^2) / 4x, x = m_r^2:
+    //   m (x - a^2 - b^2) / x - m lambda / (2 x^2)
+    const double x = mr * mr;
+    auto dk2 = [&](double a, double b, double k2) {
+      const double lam = 4.0 * x * k2;
+      return mr * (x - a * a - b * b) / x - mr * lam / (2.0 * x * x);
+    };
+    const double dq2 = dk2(m1, m2, q0 * q0), dp2 = dk2(M, m3, p0 * p0);
+    // dn/dz of the barrier numerator: 1 (L = 1), 2 z + 3 (L = 2)
+    auto dn = [&](double z) { return L == 1 ? 1.0 : (L == 2 ? 2.0 * z + 3.0 : 0.0); };
+    const double dlnR = dn(z0R) / d.nR[r] * d.r2_res * dq2;
+    const double dlnD = dn(z0D) / d.nD[r] * d.r2_D * dp2;
+    d.mass[r] = mr;
+    d.inv_width[r] = 1.0 / G;
+    d.kap1[r] = 0.5 * (dlnR + dlnD);
+    d.kap2[r] = 2.0 / mr - (2 * L + 1) * dq2 / (2.0 * q0 * q0) + dlnR;
   }
   f.m1s = (float)(m1 * m1);
   f.m2s = (float)(m2 * m2);
@@ -514,6 +531,81 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   return MIPWA_OK;
 }
 
+// NLL, gradient and d NLL / d(m_r, Gamma_r): FP64, computed Breit-Wigner terms,
+// every data and normalisation event (no cached basis, no moments).
+int evaluate_bw(mipwa_ctx* c, const double* params, double* nll, double* grad,
+                double* grad_bw) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!params || !nll || !grad || !grad_bw) return fail(c, MIPWA_EINVAL, "null pointer");
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  if (!c->data.set) return fail(c, MIPWA_ESTATE, "set_events must come first");
+  if (!c->norm.set) return fail(c, MIPWA_ESTATE, "set_norm_sample must come first");
+  if (c->data.n > 0 && c->data.dtype != c->norm.dtype)
+    return fail(c, MIPWA_EINVAL, "data and normalisation samples must share a dtype");
+  const int P = c->n_params, R = c->model.n_res;
+  for (int k = 0; k < P; ++k)
+    if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
+  const int ev32 = c->norm.dtype == MIPWA_F32;
+  const int total = c->sm_count * eval_bw_blocks_per_sm(ev32);
+  const int64_t need_d = (c->data.n + kThreads - 1) / kThreads;
+  const int64_t need_n = (c->norm.n + kThreads - 1) / kThreads;
+  int nb_d = 0;
+  if (c->data.n > 0) {
+    const double frac = (double)c->data.n / (double)(c->data.n + c->norm.n);
+    nb_d = (int)std::lround(total * frac);
+    nb_d = std::max(1, std::min(nb_d, total - 1));
+    if (nb_d > need_d) nb_d = (int)need_d;
+  }
+  int nb_n = total - nb_d;
+  if (nb_n > need_n) nb_n = (int)need_n;
+  if (nb_n < 1) nb_n = 1;
+  const int grid = nb_d + nb_n;
+  const int W = partial_width(c->model.kn.n, R, true) + 2 * R;
+  rc = ensure(c, (void**)&c->d_partials, &c->partials_cap, (size_t)grid * W * sizeof(double));
+  if (rc) return rc;
+  std::memcpy(c->h_stage, params, P * sizeof(double));
+  CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, P * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
+  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->d_coef32, c->stream);
+  CK(c, cudaGetLastError());
+  EvalArgs a;
+  a.data = c->data.cur;
+  a.norm = c->norm.cur;
+  a.n_data = c->data.n;
+  a.n_norm = c->norm.n;
+  a.nb_data = nb_d;
+  a.nb_norm = nb_n;
+  a.n_params = P;
+  a.coef = c->d_coef;
+  a.coef32 = c->d_coef32;
+  a.lu = c->d_lu;
+  a.partials = c->d_partials;
+  a.counter = c->d_counter;
+  a.out = c->d_out;
+  a.flags = c->d_flags;
+  a.basis_data = nullptr;
+  a.basis_norm = nullptr;
+  a.model = c->model;
+  CK(c, launch_eval_bw(ev32, a, grid, c->stream));
+  c->launches += 2;
+  double* h_out = c->h_stage + kStage / 2;
+  int* h_flags = (int*)(h_out + 1 + P + 2 * R);
+  CK(c, cudaMemcpyAsync(h_out, c->d_out, (1 + P + 2 * R) * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(h_flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (*h_flags & kFlagData)
+    return fail(c, MIPWA_ENONPOS, "|A|^2 <= 0 or non-finite for a data event");
+  if (*h_flags & (kFlagNorm | kFlagIntegral) || !std::isfinite(h_out[0]))
+    return fail(c, MIPWA_ENONPOS, "normalisation integral is not positive and finite");
+  *nll = h_out[0];
+  std::memcpy(grad, h_out + 1, P * sizeof(double));
+  std::memcpy(grad_bw, h_out + 1 + P, 2 * R * sizeof(double));
+  return MIPWA_OK;
+}
+
 // ----------------------------------------------------------- batched toys
 // Work list of the batched launch: normalisation items chunk-major (every toy
 // of chunk 0, then of chunk 1, ...), then each toy's data ranges.
@@ -815,6 +907,8 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   CK(c, cudaStreamSynchronize(c->stream));
   c->lu_host = lu;
   c->model = m;
+  c->r_res = r_res;
+  c->r_D = r_D;
   c->n_params = 2 * n_res + 2 * n_knots;
   c->have_model = true;
   c->tq.planned = false;
@@ -823,6 +917,31 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   rc = resort(c, c->data);
   if (rc) return rc;
   return resort(c, c->norm);
+}
+
+int mipwa_set_resonances(mipwa_ctx* c, const mipwa_resonance* res, int n_res) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  if (n_res != c->model.n_res || (n_res > 0 && !res))
+    return fail(c, MIPWA_EINVAL, "set_resonances keeps the number of resonances (%d)",
+                c->model.n_res);
+  const double thr = c->model.m1 + c->model.m2, top = c->model.mD - c->model.m2;
+  for (int r = 0; r < n_res; ++r) {
+    if (!(res[r].mass > thr && res[r].mass < top) || !(res[r].width > 0) ||
+        !std::isfinite(res[r].width) || res[r].spin < 0 || res[r].spin > 2)
+      return fail(c, MIPWA_EINVAL,
+                  "resonance %d: need m1+m2 < mass < mD-m2, width > 0, spin 0..2", r);
+  }
+  derive(c->model, res, n_res, c->r_res, c->r_D);
+  c->gram_valid = false;
+  invalidate_basis(c);
+  return MIPWA_OK;
+}
+
+int mipwa_nll_grad_bw(mipwa_ctx* c, const double* params, double* nll, double* grad,
+                      double* grad_bw) {
+  return evaluate_bw(c, params, nll, grad, grad_bw);
 }
 
 int mipwa_set_events(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, int on_device,

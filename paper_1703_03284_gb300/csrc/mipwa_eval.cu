@@ -61,9 +61,9 @@ struct Acc<float> {
 struct SmemCommon {
   float binf[kMaxSeg * 8];    // FP32 form: bins of the current flush window
   double bind[kMaxSeg * 8];   // FP64 bins of the polynomial adjoints
-  double red[kThreads / 32][1 + 2 * kMaxRes];
-  double fin_d[1 + 2 * kMaxRes + 8 * kMaxSeg];
-  double fin_n[1 + 2 * kMaxRes + 8 * kMaxSeg];
+  double red[kThreads / 32][1 + 4 * kMaxRes];
+  double fin_d[1 + 4 * kMaxRes + 8 * kMaxSeg];
+  double fin_n[1 + 4 * kMaxRes + 8 * kMaxSeg];
   double ybar[2][kMaxKnots];
   double mbar[2][kMaxKnots];
   int is_last;
@@ -371,13 +371,16 @@ __device__ __forceinline__ void flush_bins_warp(EvalSmem<T>& sm, int cur, T (&ac
 
 // Reduce partial rows in a fixed order, then -2 ln L, its gradient and the
 // adjoint of the natural-spline solve (ybar += D^T T^{-1} Mbar). Data rows are
-// [d0, d0 + dn), normalisation rows [n0, n0 + nn); writes out[0..P].
-template <typename T, bool GRAD>
+// [d0, d0 + dn), normalisation rows [n0, n0 + nn); writes out[0..P] (BWG: and
+// the derivatives with respect to the resonance masses and widths at
+// out[1 + P .. 1 + P + 2R), from 2R extra columns at the end of each row).
+template <typename T, bool GRAD, bool BWG = false>
 __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
                               const double* partials, int d0, int dn, int n0, int nn,
                               int64_t n_data, int64_t n_norm, double* out, int* flags) {
   const int R = m.n_res, N = m.kn.n, nseg = N - 1;
-  const int W = partial_width(N, R, GRAD);
+  const int W0 = partial_width(N, R, GRAD);
+  const int W = W0 + (BWG ? 2 * R : 0);
   for (int col = threadIdx.x; col < W; col += blockDim.x) {
     double sd = 0.0, sn = 0.0;
     for (int row = d0; row < d0 + dn; ++row) sd += __ldcg(&partials[(size_t)row * W + col]);
@@ -401,6 +404,7 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
       // FP32 form: the kernel accumulated against A_r / cscale_r
       const double sc = std::is_same<T, float>::value ? m.cscale[k >> 1] : 1.0;
       out[1 + k] = sm.fin_d[1 + k] * sc;
+      if constexpr (BWG) out[1 + 2 * R + 2 * N + k] = sm.fin_d[W0 + k];
     }
     // one thread per spline, in different warps
     const int sp = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 ? 1 : -1);
@@ -447,11 +451,13 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
 // row: [sum ln|A|^2 (data) or sum |A|^2 (normalisation), c_r adjoint (2R),
 // spline polynomial adjoints (8 (N-1))]. The per-evaluation model data must be
 // staged in sm; the bins are zeroed here. Every thread of the block calls this.
-template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED>
+template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false>
 __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
                                  const Cplx<T>* cached, int64_t n, int64_t first, int64_t end,
                                  int64_t stride, bool is_data, double* row, int* flags,
                                  const double* coef64) {
+  static_assert(!BWG || (std::is_same<T, double>::value && GRAD && !CACHED && SIG == 0),
+                "mass/width derivatives: FP64, direct, with the gradient");
   const int R = m.n_res, nseg = m.kn.n - 1;
   if constexpr (GRAD) {
     for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) {
@@ -462,8 +468,11 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   __syncthreads();
   Acc<T> sum;
   T gc[2 * kMaxRes];  // c_r adjoint: plain sums (gradient tolerance), FP64 per block
+  double gb[BWG ? 2 * kMaxRes : 1];  // BWG: d/dm_r, d/dGamma_r of the sum
 #pragma unroll
   for (int k = 0; k < 2 * kMaxRes; ++k) gc[k] = T(0);
+#pragma unroll
+  for (int k = 0; k < (BWG ? 2 * kMaxRes : 1); ++k) gb[k] = 0.0;
   long long sum_e = 0;  // FP32 form, data: sum of binary exponents of |A|^2
   int bad = 0;
   int iter = 0;
@@ -485,11 +494,19 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
     SwavePart<T> w12, w13;
     Cplx<T> A{T(0), T(0)};
     Cplx<T> B[kMaxRes];
+    Cplx<double> dBm[BWG ? kMaxRes : 1], dBw[BWG ? kMaxRes : 1];
     T wt = T(1);
     if (i < end) {
       const EvT e = ev[i];
       const T s12 = (T)e.x, s13 = (T)e.y;
-      A = amplitude<T, SIG, CACHED>(m, sm, s12, s13, cached, i, n, B, w12, w13);
+      if constexpr (BWG) {
+        bw_basis_deriv(m, (double)s12, (double)s13, B, dBm, dBw);
+        A = combine<kMaxRes>(m, sm, B);
+        swave_add(m, sm, s12, m.reim != 0, w12, A);
+        swave_add(m, sm, s13, m.reim != 0, w13, A);
+      } else {
+        A = amplitude<T, SIG, CACHED>(m, sm, s12, s13, cached, i, n, B, w12, w13);
+      }
       const T A2 = A.re * A.re + A.im * A.im;
       if (is_data) {
         ok = A2 > T(0) && isfinite(A2);
@@ -521,7 +538,20 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
             gc[2 * r + 1] += T(2) * wt * (A.im * B[r].re - A.re * B[r].im);
           }
         }
-        const bool reim = SIG == 0 && m.reim;
+        if constexpr (BWG) {
+#pragma unroll
+          for (int r = 0; r < kMaxRes; ++r) {
+            if (r < R) {
+              // d|A|^2/dtheta = 2 Re(conj(A) c_r dB_r/dtheta)
+              const double cr = sm.cre[r], ci = sm.cim[r];
+              const double xm = cr * dBm[r].re - ci * dBm[r].im, ym = cr * dBm[r].im + ci * dBm[r].re;
+              const double xw = cr * dBw[r].re - ci * dBw[r].im, yw = cr * dBw[r].im + ci * dBw[r].re;
+              gb[2 * r] += 2.0 * wt * (A.re * xm + A.im * ym);
+              gb[2 * r + 1] += 2.0 * wt * (A.re * xw + A.im * yw);
+            }
+          }
+        }
+        const bool reim = SIG == 0 && m.reim != 0;
         swave_adjoint(sm, w12, reim, A, wt, v);
         swave_adjoint(sm, w13, reim, A, wt, v + 8);
       } else {
@@ -566,12 +596,19 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   }
 
   // block reduction of the register sums (fixed order: shuffles, then warps)
-  const int nred = GRAD ? 1 + 2 * R : 1;
+  const int nred = GRAD ? 1 + 2 * R + (BWG ? 2 * R : 0) : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 1 + 2 * kMaxRes; ++k) {
+  for (int k = 0; k < 1 + (BWG ? 4 : 2) * kMaxRes; ++k) {
     if (k < nred) {
-      double v = k == 0 ? sum.value() + 0.69314718055994531 * (double)sum_e : (double)gc[k - 1];
+      double v = 0.0;
+      if (k == 0) {
+        v = sum.value() + 0.69314718055994531 * (double)sum_e;
+      } else if (k <= 2 * R) {
+        v = (double)gc[k - 1];
+      } else {
+        if constexpr (BWG) v = gb[k - 1 - 2 * R];
+      }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
       if (lane == 0) sm.red[warp][k] = v;
@@ -581,7 +618,9 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   if (threadIdx.x < nred) {
     double v = 0.0;
     for (int wv = 0; wv < kThreads / 32; ++wv) v += sm.red[wv][threadIdx.x];
-    row[threadIdx.x] = v;
+    const int k = threadIdx.x;
+    // BWG columns go after the polynomial adjoints
+    row[k <= 2 * R ? k : partial_width(m.kn.n, R, GRAD) + (k - 1 - 2 * R)] = v;
   }
   if constexpr (GRAD) {
     for (int k = threadIdx.x; k < nseg * 8; k += blockDim.x) row[1 + 2 * R + k] = sm.bind[k];
@@ -589,7 +628,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
 }
 
 // FP32 kernels: at most 64 registers, four 256-thread blocks per SM.
-template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED>
+template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
     eval_kernel(const EvalArgs a) {
   __shared__ EvalSmem<T> sm;
@@ -602,15 +641,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
   const EvT* ev = reinterpret_cast<const EvT*>(is_data ? a.data : a.norm);
   const Cplx<T>* cached =
       reinterpret_cast<const Cplx<T>*>(is_data ? a.basis_data : a.basis_norm);
-  const int W = partial_width(m.kn.n, m.n_res, GRAD);
+  const int W = partial_width(m.kn.n, m.n_res, GRAD) + (BWG ? 2 * m.n_res : 0);
   // each block takes one contiguous chunk (a multiple of the block size), so
   // that a thread's consecutive events lie in one spline cell
   const int64_t chunk = ((n + nb - 1) / nb + kThreads - 1) / kThreads * kThreads;
   const int64_t c0 = (int64_t)b * chunk;
   const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
-  accumulate_range<T, EvT, GRAD, SIG, CACHED>(sm, m, ev, cached, n, c0, c1, (int64_t)kThreads,
-                                              is_data, a.partials + (size_t)blockIdx.x * W,
-                                              a.flags, a.coef);
+  accumulate_range<T, EvT, GRAD, SIG, CACHED, BWG>(sm, m, ev, cached, n, c0, c1,
+                                                   (int64_t)kThreads, is_data,
+                                                   a.partials + (size_t)blockIdx.x * W, a.flags,
+                                                   a.coef);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -620,8 +660,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
   __syncthreads();
   if (!sm.is_last) return;
   __threadfence();
-  finalize_rows<T, GRAD>(sm, m, a.lu, a.partials, 0, a.nb_data, a.nb_data, a.nb_norm, a.n_data,
-                         a.n_norm, a.out, a.flags);
+  finalize_rows<T, GRAD, BWG>(sm, m, a.lu, a.partials, 0, a.nb_data, a.nb_data, a.nb_norm,
+                              a.n_data, a.n_norm, a.out, a.flags);
   if (threadIdx.x == 0) *a.counter = 0u;
 }
 
@@ -783,6 +823,23 @@ cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int grid,
                                  : run_toys<float, double2>(cached, a, grid, st);
   return ev_f32 ? run_toys<double, float2>(cached, a, grid, st)
                 : run_toys<double, double2>(cached, a, grid, st);
+}
+
+cudaError_t launch_eval_bw(int ev_f32, const EvalArgs& a, int grid, cudaStream_t st) {
+  if (ev_f32) eval_kernel<double, float2, true, 0, false, true><<<grid, kThreads, 0, st>>>(a);
+  else eval_kernel<double, double2, true, 0, false, true><<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+int eval_bw_blocks_per_sm(int ev_f32) {
+  int nb = 0;
+  if (ev_f32)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, eval_kernel<double, float2, true, 0, false, true>, kThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, eval_kernel<double, double2, true, 0, false, true>, kThreads, 0);
+  return nb > 0 ? nb : 1;
 }
 
 int toys_blocks_per_sm(int compute_f32, int ev_f32) {

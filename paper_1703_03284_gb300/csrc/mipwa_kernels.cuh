@@ -72,6 +72,10 @@ cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int grid,
 int toys_blocks_per_sm(int compute_f32, int ev_f32);
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t stream);
+// FP64 NLL + gradient + d/d(m_r, Gamma_r) (no cached basis, direct
+// normalisation); rows are partial_width() + 2R wide, out holds 1 + P + 2R.
+cudaError_t launch_eval_bw(int ev_f32, const EvalArgs& a, int grid, cudaStream_t stream);
+int eval_bw_blocks_per_sm(int ev_f32);
 // Cached Breit-Wigner basis of n events: out[r * n + i] = B_r (FP64 form) or
 // B_r / cscale_r (FP32 form), as complex double / float pairs.
 cudaError_t launch_basis(int compute_f32, int ev_f32, const Model& m, const void* ev, int64_t n,

@@ -37,6 +37,11 @@ struct ConstsD {
   double K[kMaxRes];     // g nR
   double ff[kMaxRes];    // sqrt(nR nD)
   int L[kMaxRes];
+  // derivatives with respect to the pole mass m_r and width Gamma_r:
+  //   dA_r/dGamma_r = A_r T i m_rGamma(s) / Gamma_r,
+  //   dA_r/dm_r     = A_r kap1 + A_r T (-2 m_r + i m_rGamma(s) kap2),
+  // T the propagator, kap1 = d ln sqrt(nR nD)/dm_r, kap2 = d ln K / dm_r
+  double mass[kMaxRes], inv_width[kMaxRes], kap1[kMaxRes], kap2[kMaxRes];
 };
 
 // Constants of the FP32-mixed form. Every constant that meets an input

@@ -123,3 +123,22 @@ def hessian(likelihood, p, free, h=1e-5) -> np.ndarray:
         _, gm = likelihood.nll_grad(p - e)
         H[a] = (gp[free] - gm[free]) / (2 * hs[a])
     return 0.5 * (H + H.T)
+
+
+class FreeResonances:
+    """-2 ln L over [params..., m_0, Gamma_0, ..., m_{R-1}, Gamma_{R-1}] for fits
+    in which the Breit-Wigner masses and widths float too (Sec. 2 holds them
+    fixed): each call sets the resonances and evaluates the NLL with its
+    gradient with respect to all of them (FP64)."""
+
+    def __init__(self, likelihood, spins):
+        self.lik = likelihood
+        self.spins = [int(s) for s in spins]
+
+    def nll_grad(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        R = len(self.spins)
+        p, bw = x[: len(x) - 2 * R], x[len(x) - 2 * R:]
+        self.lik.set_resonances([(bw[2 * r], bw[2 * r + 1], self.spins[r]) for r in range(R)])
+        v, g, gbw = self.lik.nll_grad_bw(p)
+        return v, np.concatenate([g, gbw])
