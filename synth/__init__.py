@@ -107,6 +107,18 @@ def kkk(n_knots: int = 40) -> ModelSpec:
                      knots=uniform_knots(lo, hi, n_knots))
 
 
+def pipipi_isobar() -> ModelSpec:
+    """Isobar baseline of the pi pi S-wave (the model a MIPWA replaces, Sec. 1-2):
+    rho(770) P, f2(1270) D and two scalar Breit-Wigner terms, f0(980) and
+    f0(1370); the spline is kept with two knots whose values are held at zero
+    (A0 = 0). The paper gives no f0 parameters: 0.990 GeV / 0.055 GeV and
+    1.350 GeV / 0.350 GeV are used."""
+    lo, hi = 0.078, 2.987
+    res = ((0.77526, 0.1491, 1), (1.2755, 0.1867, 2), (0.990, 0.055, 0), (1.350, 0.350, 0))
+    return ModelSpec(name="pipipi_isobar", mD=M_D, m1=M_PI, m2=M_PI, resonances=res,
+                     knots=(lo, hi), fixed=(0, 1, 8, 9, 10, 11))
+
+
 def as_reim(spec: ModelSpec) -> ModelSpec:
     """The same decay model with the S-wave knot values taken as real and
     imaginary parts (the complex-plane spline of Sec. 2 read literally)."""
@@ -120,6 +132,11 @@ def true_params(spec: ModelSpec) -> np.ndarray:
     if spec.name.startswith("kkk"):
         # c_phi = 0.06: the phi makes ~10 % of the rate, the S-wave the rest (Sec. 4)
         c = [0.06 + 0.0j]
+    elif spec.name == "pipipi_isobar":
+        c = [0.2 + 0.0j, 0.3 * complex(math.cos(1.0), math.sin(1.0)),
+             0.1 * complex(math.cos(0.5), math.sin(0.5)),
+             0.1 * complex(math.cos(-0.5), math.sin(-0.5))]
+        return np.array([v for z in c for v in (z.real, z.imag)] + [0.0] * (2 * spec.n_knots))
     else:
         c = [0.2 + 0.0j, 0.3 * complex(math.cos(1.0), math.sin(1.0))]
     c = (c + [0.1 + 0.0j] * spec.n_res)[: spec.n_res]
