@@ -553,6 +553,15 @@ def run(args, world, rank, local, stream):
         t64 = max_over_ranks(f0.elapsed_time(f1), world)
         kms64, kn64 = lik.kernel_time()
         lik.set_timing(False)
+        # the same FP64 evaluation with d/d(m_r, Gamma_r) of both resonances
+        lik.nll_grad_bw(params)
+        torch.cuda.synchronize()
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            lik.nll_grad_bw(params)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        tbw = max_over_ranks(f0.elapsed_time(f1), world) / args.fp64_steps
         lik.set_compute_mode(F32)
         ach64 = FLOPS_PER_EVENT_GRAD * events / (kms64 / kn64 / 1e3) / 1e12
         fp64 = {"value": world * events * args.fp64_steps / (t64 / 1e3), "unit": "events/s",
@@ -560,7 +569,10 @@ def run(args, world, rank, local, stream):
                 "roofline": {"bound": "alu", "achieved": ach64, "peak": PEAK_FP64_TFLOPS,
                              "unit": "TFLOP/s", "frac": ach64 / PEAK_FP64_TFLOPS,
                              "traffic": None, "kernel": "eval_kernel<double,float2,grad>",
-                             "peak_note": "GB300 nominal FP64, not measured"}}
+                             "peak_note": "GB300 nominal FP64, not measured"},
+                "with_bw_mass_width_derivatives": {
+                    "ms_per_step": tbw, "value": world * events / (tbw / 1e3), "unit": "events/s",
+                    "note": "NLL + gradient + d/d(m_r, Gamma_r) of both resonances, FP64"}}
 
     # ---- FP32-mixed with the cached Breit-Wigner basis (8 + 8R bytes per event)
     cached = None
