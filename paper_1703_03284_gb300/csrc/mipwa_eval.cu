@@ -16,6 +16,7 @@
 
 #include "mipwa_amp.cuh"
 #include "mipwa_kernels.cuh"
+#include "mipwa_pair.cuh"
 
 namespace mipwa {
 
@@ -124,6 +125,14 @@ struct SwavePart {
   T t, a, cs, sn;
 };
 
+// The S-wave pieces of both channels.
+template <typename T>
+struct SwaveState {
+  SwavePart<T> c12, c13;
+  __device__ int j12() const { return c12.j; }
+  __device__ int j13() const { return c13.j; }
+};
+
 // ---------------------------------------------------------------- FP64 form
 // A = sum_r c_r B_r
 template <int NR>
@@ -170,25 +179,23 @@ __device__ __forceinline__ F2 cubic_hl(const float4 hi, const float4 lo, float t
   return v;
 }
 
-// B_r / cscale_r for the FP32 form (SIG: compile-time resonance spins, or 0).
+// B_r / cscale_r for the FP32 form (SIG: compile-time resonance spins, or 0),
+// both channels in the two lanes of packed pairs.
 template <int SIG>
 __device__ __forceinline__ void bw_basis(const Model& m, float s12, float s13, Cplx<float>* B) {
   const ConstsF& c = m.cf;
-  const ChanF k12 = channel_f(c, s12);
-  const ChanF k13 = channel_f(c, s13);
-  F2 z1a, z1b;
-  float z2a, z2b;
-  zemach_f(c, k12, s13, z1a, z2a);
-  zemach_f(c, k13, s12, z1b, z2b);
+  const ChanP k = channel_p(c, P2{s12, s13});
+  F2P z1;
+  P2 z2;
+  zemach_p(c, k, P2{s13, s12}, z1, z2);
   constexpr int NR = SIG ? sig_count(SIG) : kMaxRes;
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     if (SIG || r < m.n_res) {
       const int L = SIG ? sig_L(SIG, r) : c.L[r];
-      const Cplx<float> u = bw_f(c, r, L, k12, z1a, z2a);
-      const Cplx<float> v = bw_f(c, r, L, k13, z1b, z2b);
-      B[r].re = u.re + v.re;
-      B[r].im = u.im + v.im;
+      const CplxP u = bw_p(c, r, L, k, z1, z2);
+      B[r].re = u.re.x + u.re.y;
+      B[r].im = u.im.x + u.im.y;
     }
   }
 }
@@ -232,7 +239,7 @@ __device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<float>&
 template <typename T, int SIG, bool CACHED>
 __device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& sm, T s12, T s13,
                                              const Cplx<T>* cached, int64_t i, int64_t n,
-                                             Cplx<T>* B, SwavePart<T>& w12, SwavePart<T>& w13) {
+                                             Cplx<T>* B, SwaveState<T>& w) {
   constexpr int NR = SIG ? sig_count(SIG) : kMaxRes;
   if constexpr (CACHED) {
 #pragma unroll
@@ -245,8 +252,8 @@ __device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& 
   }
   Cplx<T> A = combine<NR>(m, sm, B);
   const bool reim = SIG == 0 && m.reim;  // the specialised kernels serve magnitude/phase only
-  swave_add(m, sm, s12, reim, w12, A);
-  swave_add(m, sm, s13, reim, w13, A);
+  swave_add(m, sm, s12, reim, w.c12, A);
+  swave_add(m, sm, s13, reim, w.c13, A);
   return A;
 }
 
@@ -491,7 +498,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   for (int64_t base = first; base < end; base += stride) {
     const int64_t i = base + threadIdx.x;
     bool ok = false;
-    SwavePart<T> w12, w13;
+    SwaveState<T> sw;
     Cplx<T> A{T(0), T(0)};
     Cplx<T> B[kMaxRes];
     Cplx<double> dBm[BWG ? kMaxRes : 1], dBw[BWG ? kMaxRes : 1];
@@ -502,10 +509,10 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
       if constexpr (BWG) {
         bw_basis_deriv(m, (double)s12, (double)s13, B, dBm, dBw);
         A = combine<kMaxRes>(m, sm, B);
-        swave_add(m, sm, s12, m.reim != 0, w12, A);
-        swave_add(m, sm, s13, m.reim != 0, w13, A);
+        swave_add(m, sm, s12, m.reim != 0, sw.c12, A);
+        swave_add(m, sm, s13, m.reim != 0, sw.c13, A);
       } else {
-        A = amplitude<T, SIG, CACHED>(m, sm, s12, s13, cached, i, n, B, w12, w13);
+        A = amplitude<T, SIG, CACHED>(m, sm, s12, s13, cached, i, n, B, sw);
       }
       const T A2 = A.re * A.re + A.im * A.im;
       if (is_data) {
@@ -552,15 +559,15 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
           }
         }
         const bool reim = SIG == 0 && m.reim != 0;
-        swave_adjoint(sm, w12, reim, A, wt, v);
-        swave_adjoint(sm, w13, reim, A, wt, v + 8);
+        swave_adjoint(sm, sw.c12, reim, A, wt, v);
+        swave_adjoint(sm, sw.c13, reim, A, wt, v + 8);
       } else {
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = T(0);
       }
       if constexpr (kThreadBins) {
         if (ok) {
-          const int key = (w12.j << 6) | w13.j;
+          const int key = (sw.j12() << 6) | sw.j13();
           if (key != cur) {
             if (cur >= 0) flush_bins(sm, cur, acc);
             cur = key;
@@ -573,7 +580,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
           flush_bins_warp(sm, cur, acc);
         }
       } else {
-        bin_swave_warp(sm, ok, ok ? w12.j : 0, ok ? w13.j : 0, v);
+        bin_swave_warp(sm, ok, ok ? sw.j12() : 0, ok ? sw.j13() : 0, v);
       }
     }
     if constexpr (GRAD && std::is_same<T, float>::value) {
@@ -724,9 +731,8 @@ __global__ void __launch_bounds__(kThreads) amp2_kernel(const Model m, const dou
     double v = 0.0;
     if (inside_plot(m, (double)e.x, (double)e.y)) {
       Cplx<T> B[kMaxRes];
-      SwavePart<T> w12, w13;
-      const Cplx<T> A =
-          amplitude<T, 0, false>(m, sm, (T)e.x, (T)e.y, nullptr, 0, 0, B, w12, w13);
+      SwaveState<T> sw;
+      const Cplx<T> A = amplitude<T, 0, false>(m, sm, (T)e.x, (T)e.y, nullptr, 0, 0, B, sw);
       v = (double)(A.re * A.re + A.im * A.im);
     }
     out[i] = v;
