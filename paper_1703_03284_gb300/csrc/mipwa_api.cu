@@ -274,16 +274,15 @@ int grid_for(mipwa_ctx* c, int64_t n) {
   return g < 1 ? 1 : (int)g;
 }
 
-// Reorder the events of `src` (n of them) into `dst` grouped by spline cell.
-int sort_into(mipwa_ctx* c, const void* src, int64_t n, int dtype, void* dst) {
+int ensure_sortwork(mipwa_ctx* c) {
   size_t ints = 0;
   sort_workspace_ints(c->model.kn.n, &ints);
-  int rc = ensure(c, (void**)&c->d_sortwork, &c->sortwork_cap, ints * sizeof(int));
-  if (rc) return rc;
-  CK(c, launch_sort(dtype == MIPWA_F32, c->model.kn, src, n, dst, c->d_sortwork, c->stream));
-  c->launches += 5;
-  return MIPWA_OK;
+  return ensure(c, (void**)&c->d_sortwork, &c->sortwork_cap, ints * sizeof(int));
 }
+
+// Kernel launches of one two-pass sort: per pass a count, three offset
+// kernels and a scatter.
+constexpr int kSortLaunches = 10;
 
 bool sortable(int64_t n) { return n > 1 && n < (int64_t)0x7fffffff; }
 
@@ -357,6 +356,7 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
   const size_t bytes = (size_t)n * ev_bytes(dtype);
   rc = ensure(c, &smp.spare, &smp.spare_cap, bytes);
   if (rc) return rc;
+  const bool will_sort = c->have_model && sortable(n) && !smp.no_sort;
   unsigned long long outside = 0;
   if (n > 0) {
     if (on_device) {
@@ -367,8 +367,16 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
       CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyHostToDevice, c->stream));
     }
     CK(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream));
-    CK(c, launch_inside(dtype == MIPWA_F32, c->model, smp.spare, n, nullptr, c->d_count,
-                        grid_for(c, n), c->stream));
+    if (will_sort) {
+      // the first counting pass of the sort also counts the outside events
+      rc = ensure_sortwork(c);
+      if (rc) return rc;
+      CK(c, launch_sort_count_checked(dtype == MIPWA_F32, c->model, smp.spare, n,
+                                      c->d_sortwork, c->d_count, c->stream));
+    } else {
+      CK(c, launch_inside(dtype == MIPWA_F32, c->model, smp.spare, n, nullptr, c->d_count,
+                          grid_for(c, n), c->stream));
+    }
     c->launches++;
     CK(c, cudaMemcpyAsync(&outside, c->d_count, sizeof(outside), cudaMemcpyDeviceToHost,
                           c->stream));
@@ -380,13 +388,17 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
                 (long long)n);
   }
   smp.sorted = false;
-  if (c->have_model && sortable(n) && !smp.no_sort) {
-    // the old sample is no longer needed: sort the validated copy into it
+  if (will_sort) {
+    // the old sample is no longer needed: it takes the first pass, and the
+    // validated copy the final order
     rc = ensure(c, &smp.cur, &smp.cur_cap, bytes);
     if (rc) return rc;
-    rc = sort_into(c, smp.spare, n, dtype, smp.cur);
-    if (rc) return rc;
+    CK(c, launch_sort_rest(dtype == MIPWA_F32, c->model, smp.spare, n, smp.cur, smp.spare,
+                           c->d_sortwork, c->stream));
+    c->launches += kSortLaunches - 1;
     CK(c, cudaStreamSynchronize(c->stream));
+    std::swap(smp.cur, smp.spare);
+    std::swap(smp.cur_cap, smp.spare_cap);
     smp.sorted = true;
   } else {
     std::swap(smp.cur, smp.spare);
@@ -405,12 +417,12 @@ int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
   if (!smp.set || !sortable(smp.n) || smp.no_sort) return MIPWA_OK;
   const size_t bytes = (size_t)smp.n * ev_bytes(smp.dtype);
   int rc = ensure(c, &smp.spare, &smp.spare_cap, bytes);
+  if (!rc) rc = ensure_sortwork(c);
   if (rc) return rc;
-  rc = sort_into(c, smp.cur, smp.n, smp.dtype, smp.spare);
-  if (rc) return rc;
+  CK(c, launch_sort(smp.dtype == MIPWA_F32, c->model, smp.cur, smp.n, smp.spare, smp.cur,
+                    c->d_sortwork, c->stream));
+  c->launches += kSortLaunches;
   CK(c, cudaStreamSynchronize(c->stream));
-  std::swap(smp.cur, smp.spare);
-  std::swap(smp.cur_cap, smp.spare_cap);
   smp.sorted = true;
   smp.basis_valid = false;
   return MIPWA_OK;

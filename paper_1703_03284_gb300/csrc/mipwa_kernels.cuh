@@ -88,11 +88,20 @@ cudaError_t launch_inside(int ev_f32, const Model& m, const void* ev, int64_t n,
 // Blocks per SM of the event kernel that runs for this model and form.
 int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached);
 
-// Stable counting sort of n events from src into dst by spline cell (j12, j13);
-// work holds sort_workspace_ints() ints. n must be below 2^31.
+// Stable sort of n events from src into dst by spline cell (j12, j13), in two
+// counting passes through tmp (n events; src may equal dst, not tmp); work
+// holds sort_workspace_ints() ints. n must be below 2^31.
 cudaError_t sort_workspace_ints(int n_knots, size_t* ints);
-cudaError_t launch_sort(int ev_f32, const Knots& kn, const void* src, int64_t n, void* dst,
-                        int* work, cudaStream_t stream);
+cudaError_t launch_sort(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
+                        void* dst, int* work, cudaStream_t stream);
+// The same split at the first count, which also adds the number of events
+// outside the Dalitz plot to *outside (device): validate, then finish with
+// launch_sort_rest (nothing is written before it).
+cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* src, int64_t n,
+                                      int* work, unsigned long long* outside,
+                                      cudaStream_t stream);
+cudaError_t launch_sort_rest(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
+                             void* dst, int* work, cudaStream_t stream);
 // Index range [first[k], last[k]) of every spline cell k = j12 (N-1) + j13 in
 // a sample grouped by cell (n < 2^31); empty cells get [0, 0).
 cudaError_t launch_cell_bounds(int ev_f32, const Knots& kn, const void* ev, int64_t n, int* first,

@@ -3,12 +3,19 @@
 // -2 ln L and its gradient are sums over events, so the library may store
 // events in any order. Grouping them by the pair of S-wave segments they fall
 // in makes every warp of the event kernels see one (j12, j13) cell almost
-// always: the cubic coefficients become shared-memory broadcasts and the
-// spline adjoint can be reduced across the warp before it is binned.
+// always: the cubic coefficients become shared-memory broadcasts and the spline
+// adjoint can be reduced across the warp before it is binned.
 //
-// The sort is a stable counting sort (deterministic for a given input):
+// Two passes of a stable counting sort (deterministic for a given input): by
+// j12 alone, then by the cell key j12 (N-1) + j13. The result is the single
+// sort by cell key (both passes are stable), but every write goes to a long
+// run: in the first pass a chunk of events spreads over N-1 keys only, and in
+// the second a chunk lies almost entirely in one j12 bucket, so it again
+// meets about N-1 keys (a single pass spreads each chunk over (N-1)^2 keys and
+// writes runs of a few events). Each pass:
 //   1. count:   each block counts the keys of its contiguous chunk into its
-//               own row of a [block][key] table;
+//               own row of a [block][key] table (the first pass of a new
+//               sample also counts the events outside the Dalitz plot);
 //   2. offsets: the table becomes, in place, each (block, key)'s first output
 //               position: all events of lower keys, plus the events of the
 //               same key in earlier blocks (column sums over groups of
@@ -44,23 +51,53 @@ __device__ __forceinline__ int key_of(const Knots& kn, const EvT& e) {
   return cell_key_general(kn, kn.s, e);
 }
 
+// Sort key of a pass: the cell key (FULL) or its j12 part.
+template <typename EvT, bool FULL>
+__device__ __forceinline__ int pass_key(const Knots& kn, const EvT& e) {
+  const int k = key_of(kn, e);
+  return FULL ? k : k / (kn.n - 1);
+}
+
+template <bool FULL>
+__host__ __device__ inline int pass_keys(int n_knots) {
+  return FULL ? (n_knots - 1) * (n_knots - 1) : n_knots - 1;
+}
+
 __host__ __device__ inline int64_t chunk_begin(int64_t n, int b) {
   const int64_t per = (n + kSortBlocks - 1) / kSortBlocks;
   const int64_t v = per * b;
   return v < n ? v : n;
 }
 
-template <typename EvT>
-__global__ void __launch_bounds__(32) sort_count_kernel(const Knots kn, const EvT* ev, int64_t n,
-                                                        int* counts /* [kSortBlocks][nkeys] */) {
+// CHECK: also count the events outside the Dalitz plot into *outside (their
+// keys are clamped segments, so the histogram stays in range).
+template <typename EvT, bool FULL, bool CHECK>
+__global__ void __launch_bounds__(32) sort_count_kernel(const Model m, const EvT* ev, int64_t n,
+                                                        int* counts /* [kSortBlocks][nkeys] */,
+                                                        unsigned long long* outside) {
   extern __shared__ int hist[];
-  const int nkeys = (kn.n - 1) * (kn.n - 1);
+  const Knots& kn = m.kn;
+  const int nkeys = pass_keys<FULL>(kn.n);
   for (int k = threadIdx.x; k < nkeys; k += 32) hist[k] = 0;
   __syncwarp();
   const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
-  for (int64_t i = b0 + threadIdx.x; i < b1; i += 32) atomicAdd(&hist[key_of(kn, ev[i])], 1);
+  unsigned int out = 0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += 32) {
+    const EvT e = ev[i];
+    atomicAdd(&hist[pass_key<EvT, FULL>(kn, e)], 1);
+    if constexpr (CHECK) {
+      bool in;
+      if constexpr (std::is_same<EvT, float2>::value) in = inside_plot_fast(m, e.x, e.y);
+      else in = inside_plot(m, e.x, e.y);
+      out += in ? 0u : 1u;
+    }
+  }
   __syncwarp();
   for (int k = threadIdx.x; k < nkeys; k += 32) counts[(size_t)blockIdx.x * nkeys + k] = hist[k];
+  if constexpr (CHECK) {
+    for (int off = 16; off > 0; off >>= 1) out += __shfl_down_sync(0xffffffffu, out, off);
+    if (threadIdx.x == 0 && out) atomicAdd(outside, (unsigned long long)out);
+  }
 }
 
 constexpr int kGroup = 64;                        // blocks per column-sum group
@@ -139,11 +176,11 @@ __global__ void __launch_bounds__(256) sort_offsets(int* counts, int nkeys, cons
   }
 }
 
-template <typename EvT>
+template <typename EvT, bool FULL>
 __global__ void __launch_bounds__(32) sort_scatter_kernel(const Knots kn, const EvT* src, int64_t n,
                                                           const int* offsets, EvT* dst) {
   extern __shared__ int cursor[];
-  const int nkeys = (kn.n - 1) * (kn.n - 1);
+  const int nkeys = pass_keys<FULL>(kn.n);
   for (int k = threadIdx.x; k < nkeys; k += 32)
     cursor[k] = offsets[(size_t)blockIdx.x * nkeys + k];
   __syncwarp();
@@ -157,7 +194,7 @@ __global__ void __launch_bounds__(32) sort_scatter_kernel(const Knots kn, const 
     int key = -1 - (int)threadIdx.x;  // distinct dummy keys for idle lanes
     if (live) {
       e = src[i];
-      key = key_of(kn, e);
+      key = pass_key<EvT, FULL>(kn, e);
     }
     const unsigned same = __match_any_sync(0xffffffffu, key) & active;
     if (live) {
@@ -205,31 +242,62 @@ cudaError_t sort_workspace_ints(int n_knots, size_t* ints) {
   return cudaSuccess;
 }
 
-template <typename EvT>
-static cudaError_t sort_impl(const Knots& kn, const EvT* src, int64_t n, EvT* dst, int* work,
-                             cudaStream_t st) {
-  const int nkeys = (kn.n - 1) * (kn.n - 1);
+template <typename EvT, bool FULL, bool CHECK>
+static cudaError_t count_pass(const Model& m, const EvT* src, int64_t n, int* work,
+                              unsigned long long* outside, cudaStream_t st) {
+  const size_t smem = (size_t)pass_keys<FULL>(m.kn.n) * sizeof(int);
+  sort_count_kernel<EvT, FULL, CHECK><<<kSortBlocks, 32, smem, st>>>(m, src, n, work, outside);
+  return cudaGetLastError();
+}
+
+// Offsets and scatter of one pass whose counts are in `work`.
+template <typename EvT, bool FULL>
+static cudaError_t finish_pass(const Knots& kn, const EvT* src, int64_t n, EvT* dst, int* work,
+                               cudaStream_t st) {
+  const int nkeys = pass_keys<FULL>(kn.n);
   const size_t smem = (size_t)nkeys * sizeof(int);
-  sort_count_kernel<EvT><<<kSortBlocks, 32, smem, st>>>(kn, src, n, work);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   int* group_sum = work + (size_t)nkeys * kSortBlocks;
   int* key_start = group_sum + (size_t)nkeys * kGroups;
   const dim3 cgrid((nkeys + 255) / 256, kGroups);
   sort_group_sums<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum);
   sort_key_starts<<<1, 1024, 0, st>>>(group_sum, nkeys, key_start);
   sort_offsets<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum, key_start);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  sort_scatter_kernel<EvT><<<kSortBlocks, 32, smem, st>>>(kn, src, n, work, dst);
+  sort_scatter_kernel<EvT, FULL><<<kSortBlocks, 32, smem, st>>>(kn, src, n, work, dst);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(int ev_f32, const Knots& kn, const void* src, int64_t n, void* dst,
-                        int* work, cudaStream_t st) {
+// Both passes after the first count: src -> tmp by j12, tmp -> dst by cell.
+template <typename EvT>
+static cudaError_t sort_rest(const Model& m, const EvT* src, int64_t n, EvT* tmp, EvT* dst,
+                             int* work, cudaStream_t st) {
+  cudaError_t e = finish_pass<EvT, false>(m.kn, src, n, tmp, work, st);
+  if (e == cudaSuccess) e = count_pass<EvT, true, false>(m, tmp, n, work, nullptr, st);
+  if (e == cudaSuccess) e = finish_pass<EvT, true>(m.kn, tmp, n, dst, work, st);
+  return e;
+}
+
+cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* src, int64_t n,
+                                      int* work, unsigned long long* outside, cudaStream_t st) {
+  if (ev_f32) return count_pass<float2, false, true>(m, (const float2*)src, n, work, outside, st);
+  return count_pass<double2, false, true>(m, (const double2*)src, n, work, outside, st);
+}
+
+cudaError_t launch_sort_rest(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
+                             void* dst, int* work, cudaStream_t st) {
   if (ev_f32)
-    return sort_impl(kn, (const float2*)src, n, (float2*)dst, work, st);
-  return sort_impl(kn, (const double2*)src, n, (double2*)dst, work, st);
+    return sort_rest(m, (const float2*)src, n, (float2*)tmp, (float2*)dst, work, st);
+  return sort_rest(m, (const double2*)src, n, (double2*)tmp, (double2*)dst, work, st);
+}
+
+cudaError_t launch_sort(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
+                        void* dst, int* work, cudaStream_t st) {
+  cudaError_t e;
+  if (ev_f32) e = count_pass<float2, false, false>(m, (const float2*)src, n, work, nullptr, st);
+  else e = count_pass<double2, false, false>(m, (const double2*)src, n, work, nullptr, st);
+  if (e != cudaSuccess) return e;
+  return launch_sort_rest(ev_f32, m, src, n, tmp, dst, work, st);
 }
 
 }  // namespace mipwa
