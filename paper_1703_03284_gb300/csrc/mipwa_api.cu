@@ -54,7 +54,12 @@ struct mipwa_ctx {
     size_t basis_cap = 0;
     bool basis_valid = false;
     bool no_sort = false;   // keep the caller's order (toy ranges)
+    cudaEvent_t spare_free = nullptr;  // recorded after the last kernel that touches `spare`
   } data, norm, toys;
+  // host-to-device copies of new samples run here, so that one sample's copy
+  // overlaps the previous sample's sort on the context stream
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_done = nullptr;
   bool basis_on = false;
   // Re/Im form: normalisation from per-cell moments of the normalisation sample
   bool gram_on = false;
@@ -364,7 +369,13 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
         return fail(c, MIPWA_EINVAL, "on_device set but the pointer is not device memory");
       CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
     } else {
-      CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyHostToDevice, c->stream));
+      // on the copy stream, after the last kernel that used this sample's
+      // spare buffer, so that it overlaps other work still running on the
+      // context stream (another sample's sort); the context stream waits for it
+      CK(c, cudaStreamWaitEvent(c->copy_stream, smp.spare_free, 0));
+      CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyHostToDevice, c->copy_stream));
+      CK(c, cudaEventRecord(c->copy_done, c->copy_stream));
+      CK(c, cudaStreamWaitEvent(c->stream, c->copy_done, 0));
     }
     CK(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream));
     if (will_sort) {
@@ -396,13 +407,16 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
     CK(c, launch_sort_rest(dtype == MIPWA_F32, c->model, smp.spare, n, smp.cur, smp.spare,
                            c->d_sortwork, c->stream));
     c->launches += kSortLaunches - 1;
-    CK(c, cudaStreamSynchronize(c->stream));
+    // no wait: later work on the context stream is ordered after the sort, and
+    // the next copy into this sample's spare buffer waits for this event
+    CK(c, cudaEventRecord(smp.spare_free, c->stream));
     std::swap(smp.cur, smp.spare);
     std::swap(smp.cur_cap, smp.spare_cap);
     smp.sorted = true;
   } else {
     std::swap(smp.cur, smp.spare);
     std::swap(smp.cur_cap, smp.spare_cap);
+    CK(c, cudaEventRecord(smp.spare_free, c->stream));
   }
   smp.n = n;
   smp.dtype = dtype;
@@ -422,6 +436,7 @@ int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
   CK(c, launch_sort(smp.dtype == MIPWA_F32, c->model, smp.cur, smp.n, smp.spare, smp.cur,
                     c->d_sortwork, c->stream));
   c->launches += kSortLaunches;
+  CK(c, cudaEventRecord(smp.spare_free, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   smp.sorted = true;
   smp.basis_valid = false;
@@ -805,6 +820,14 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
   if (cudaMemset(c->d_counter, 0, sizeof(unsigned int)) != cudaSuccess) return bail(MIPWA_ECUDA);
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
     return bail(MIPWA_ECUDA);
+  if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming) != cudaSuccess)
+    return bail(MIPWA_ECUDA);
+  for (mipwa_ctx::Sample* smp : {&c->data, &c->norm, &c->toys}) {
+    if (cudaEventCreateWithFlags(&smp->spare_free, cudaEventDisableTiming) != cudaSuccess)
+      return bail(MIPWA_ECUDA);
+    if (cudaEventRecord(smp->spare_free, c->stream) != cudaSuccess) return bail(MIPWA_ECUDA);
+  }
   *out = c;
   return MIPWA_OK;
 }
@@ -813,6 +836,7 @@ void mipwa_destroy(mipwa_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   for (void* p : {(void*)c->d_lu, (void*)c->d_params, (void*)c->d_coef, (void*)c->d_coef32,
                   (void*)c->d_out,
                   (void*)c->d_flags, (void*)c->d_counter, (void*)c->d_count,
@@ -832,6 +856,10 @@ void mipwa_destroy(mipwa_ctx* c) {
   if (c->tq.h_out) cudaFreeHost(c->tq.h_out);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (mipwa_ctx::Sample* smp : {&c->data, &c->norm, &c->toys})
+    if (smp->spare_free) cudaEventDestroy(smp->spare_free);
+  if (c->copy_done) cudaEventDestroy(c->copy_done);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }

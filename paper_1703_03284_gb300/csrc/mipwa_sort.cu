@@ -13,15 +13,17 @@
 // the second a chunk lies almost entirely in one j12 bucket, so it again
 // meets about N-1 keys (a single pass spreads each chunk over (N-1)^2 keys and
 // writes runs of a few events). Each pass:
-//   1. count:   each block counts the keys of its contiguous chunk into its
-//               own row of a [block][key] table (the first pass of a new
+//   1. count:   each warp counts the keys of its contiguous chunk into its
+//               own row of a [chunk][key] table (the first pass of a new
 //               sample also counts the events outside the Dalitz plot);
 //   2. offsets: the table becomes, in place, each (block, key)'s first output
 //               position: all events of lower keys, plus the events of the
 //               same key in earlier blocks (column sums over groups of
 //               blocks, one scan over keys, then the running sums per group);
-//   3. scatter: each block walks its chunk in order, one warp at a time, and
+//   3. scatter: each warp walks its chunk in order, 32 events at a time, and
 //               places each event at its key's running offset.
+// Eight chunks share a thread block (each warp its own shared-memory table),
+// so that twice as many chunks are resident per SM as with one-warp blocks.
 #include <cuda_runtime.h>
 
 #include "mipwa_amp.cuh"
@@ -30,6 +32,7 @@
 namespace mipwa {
 
 constexpr int kSortBlocks = 8192;  // chunks (one warp each); a multiple of kGroup
+constexpr int kSortWarps = 8;      // chunks per thread block (one warp each)
 
 template <typename EvT>
 __device__ __forceinline__ int cell_key_general(const Knots& kn, const double* knot, const EvT& e) {
@@ -72,17 +75,19 @@ __host__ __device__ inline int64_t chunk_begin(int64_t n, int b) {
 // CHECK: also count the events outside the Dalitz plot into *outside (their
 // keys are clamped segments, so the histogram stays in range).
 template <typename EvT, bool FULL, bool CHECK>
-__global__ void __launch_bounds__(32) sort_count_kernel(const Model m, const EvT* ev, int64_t n,
-                                                        int* counts /* [kSortBlocks][nkeys] */,
-                                                        unsigned long long* outside) {
-  extern __shared__ int hist[];
+__global__ void __launch_bounds__(32 * kSortWarps)
+    sort_count_kernel(const Model m, const EvT* ev, int64_t n,
+                      int* counts /* [kSortBlocks][nkeys] */, unsigned long long* outside) {
+  extern __shared__ int hist_all[];
   const Knots& kn = m.kn;
   const int nkeys = pass_keys<FULL>(kn.n);
-  for (int k = threadIdx.x; k < nkeys; k += 32) hist[k] = 0;
+  const int lane = threadIdx.x & 31, chunk = blockIdx.x * kSortWarps + (threadIdx.x >> 5);
+  int* hist = hist_all + (threadIdx.x >> 5) * nkeys;
+  for (int k = lane; k < nkeys; k += 32) hist[k] = 0;
   __syncwarp();
-  const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
+  const int64_t b0 = chunk_begin(n, chunk), b1 = chunk_begin(n, chunk + 1);
   unsigned int out = 0;
-  for (int64_t i = b0 + threadIdx.x; i < b1; i += 32) {
+  for (int64_t i = b0 + lane; i < b1; i += 32) {
     const EvT e = ev[i];
     atomicAdd(&hist[pass_key<EvT, FULL>(kn, e)], 1);
     if constexpr (CHECK) {
@@ -93,10 +98,10 @@ __global__ void __launch_bounds__(32) sort_count_kernel(const Model m, const EvT
     }
   }
   __syncwarp();
-  for (int k = threadIdx.x; k < nkeys; k += 32) counts[(size_t)blockIdx.x * nkeys + k] = hist[k];
+  for (int k = lane; k < nkeys; k += 32) counts[(size_t)chunk * nkeys + k] = hist[k];
   if constexpr (CHECK) {
     for (int off = 16; off > 0; off >>= 1) out += __shfl_down_sync(0xffffffffu, out, off);
-    if (threadIdx.x == 0 && out) atomicAdd(outside, (unsigned long long)out);
+    if (lane == 0 && out) atomicAdd(outside, (unsigned long long)out);
   }
 }
 
@@ -177,21 +182,22 @@ __global__ void __launch_bounds__(256) sort_offsets(int* counts, int nkeys, cons
 }
 
 template <typename EvT, bool FULL>
-__global__ void __launch_bounds__(32) sort_scatter_kernel(const Knots kn, const EvT* src, int64_t n,
-                                                          const int* offsets, EvT* dst) {
-  extern __shared__ int cursor[];
+__global__ void __launch_bounds__(32 * kSortWarps)
+    sort_scatter_kernel(const Knots kn, const EvT* src, int64_t n, const int* offsets, EvT* dst) {
+  extern __shared__ int cursor_all[];
   const int nkeys = pass_keys<FULL>(kn.n);
-  for (int k = threadIdx.x; k < nkeys; k += 32)
-    cursor[k] = offsets[(size_t)blockIdx.x * nkeys + k];
+  const int lane = threadIdx.x & 31, chunk = blockIdx.x * kSortWarps + (threadIdx.x >> 5);
+  int* cursor = cursor_all + (threadIdx.x >> 5) * nkeys;
+  for (int k = lane; k < nkeys; k += 32) cursor[k] = offsets[(size_t)chunk * nkeys + k];
   __syncwarp();
-  const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
-  const unsigned lane_lt = (1u << threadIdx.x) - 1u;
+  const int64_t b0 = chunk_begin(n, chunk), b1 = chunk_begin(n, chunk + 1);
+  const unsigned lane_lt = (1u << lane) - 1u;
   for (int64_t base = b0; base < b1; base += 32) {
-    const int64_t i = base + threadIdx.x;
+    const int64_t i = base + lane;
     const bool live = i < b1;
     const unsigned active = __ballot_sync(0xffffffffu, live);
     EvT e{};
-    int key = -1 - (int)threadIdx.x;  // distinct dummy keys for idle lanes
+    int key = -1 - lane;  // distinct dummy keys for idle lanes
     if (live) {
       e = src[i];
       key = pass_key<EvT, FULL>(kn, e);
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(32) sort_scatter_kernel(const Knots kn, const 
       const int base_pos = cursor[key];
       dst[base_pos + rank] = e;
       __syncwarp(same);
-      if ((int)threadIdx.x == leader) cursor[key] = base_pos + __popc(same);
+      if (lane == leader) cursor[key] = base_pos + __popc(same);
     }
     __syncwarp();
   }
@@ -245,8 +251,11 @@ cudaError_t sort_workspace_ints(int n_knots, size_t* ints) {
 template <typename EvT, bool FULL, bool CHECK>
 static cudaError_t count_pass(const Model& m, const EvT* src, int64_t n, int* work,
                               unsigned long long* outside, cudaStream_t st) {
-  const size_t smem = (size_t)pass_keys<FULL>(m.kn.n) * sizeof(int);
-  sort_count_kernel<EvT, FULL, CHECK><<<kSortBlocks, 32, smem, st>>>(m, src, n, work, outside);
+  const size_t smem = (size_t)kSortWarps * pass_keys<FULL>(m.kn.n) * sizeof(int);
+  auto kern = sort_count_kernel<EvT, FULL, CHECK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<kSortBlocks / kSortWarps, 32 * kSortWarps, smem, st>>>(m, src, n, work, outside);
   return cudaGetLastError();
 }
 
@@ -255,7 +264,7 @@ template <typename EvT, bool FULL>
 static cudaError_t finish_pass(const Knots& kn, const EvT* src, int64_t n, EvT* dst, int* work,
                                cudaStream_t st) {
   const int nkeys = pass_keys<FULL>(kn.n);
-  const size_t smem = (size_t)nkeys * sizeof(int);
+  const size_t smem = (size_t)kSortWarps * nkeys * sizeof(int);
   int* group_sum = work + (size_t)nkeys * kSortBlocks;
   int* key_start = group_sum + (size_t)nkeys * kGroups;
   const dim3 cgrid((nkeys + 255) / 256, kGroups);
@@ -264,7 +273,10 @@ static cudaError_t finish_pass(const Knots& kn, const EvT* src, int64_t n, EvT* 
   sort_offsets<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum, key_start);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  sort_scatter_kernel<EvT, FULL><<<kSortBlocks, 32, smem, st>>>(kn, src, n, work, dst);
+  auto kern = sort_scatter_kernel<EvT, FULL>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<kSortBlocks / kSortWarps, 32 * kSortWarps, smem, st>>>(kn, src, n, work, dst);
   return cudaGetLastError();
 }
 
