@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--n-events", type=int, default=100_000_000,
                     help="data events (= normalisation events)")
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cached-steps", type=int, default=10)
     ap.add_argument("--toys-steps", type=int, default=3)
     ap.add_argument("--reim-steps", type=int, default=10)

@@ -35,6 +35,11 @@ __host__ __device__ constexpr int sig_L(int sig, int r) {
 }
 constexpr int kSigPD = 23;
 static_assert(sig_count(kSigPD) == 2 && sig_L(kSigPD, 0) == 1 && sig_L(kSigPD, 1) == 2, "sig");
+// A signature plus kSigReim: the same spins with the Re/Im S-wave form.
+constexpr int kSigReim = 1000;
+constexpr int kSigPDReim = kSigReim + kSigPD;
+__host__ __device__ constexpr int sig_spins(int sig) { return sig % kSigReim; }
+__host__ __device__ constexpr bool sig_reim(int sig) { return sig >= kSigReim; }
 
 // Per-thread running sums: plain FP64, or Kahan-compensated FP32.
 template <typename T>
@@ -188,11 +193,12 @@ __device__ __forceinline__ void bw_basis(const Model& m, float s12, float s13, C
   F2P z1;
   P2 z2;
   zemach_p(c, k, P2{s13, s12}, z1, z2);
-  constexpr int NR = SIG ? sig_count(SIG) : kMaxRes;
+  constexpr int SP = sig_spins(SIG);
+  constexpr int NR = SP ? sig_count(SP) : kMaxRes;
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
-    if (SIG || r < m.n_res) {
-      const int L = SIG ? sig_L(SIG, r) : c.L[r];
+    if (SP || r < m.n_res) {
+      const int L = SP ? sig_L(SP, r) : c.L[r];
       const CplxP u = bw_p(c, r, L, k, z1, z2);
       B[r].re = u.re.x + u.re.y;
       B[r].im = u.im.x + u.im.y;
@@ -240,18 +246,20 @@ template <typename T, int SIG, bool CACHED>
 __device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& sm, T s12, T s13,
                                              const Cplx<T>* cached, int64_t i, int64_t n,
                                              Cplx<T>* B, SwaveState<T>& w) {
-  constexpr int NR = SIG ? sig_count(SIG) : kMaxRes;
+  constexpr int SP = sig_spins(SIG);
+  constexpr int NR = SP ? sig_count(SP) : kMaxRes;
   if constexpr (CACHED) {
 #pragma unroll
     for (int r = 0; r < NR; ++r)
       if (r < m.n_res) B[r] = cached[(int64_t)r * n + i];
   } else if constexpr (std::is_same<T, float>::value) {
-    bw_basis<SIG>(m, s12, s13, B);
+    bw_basis<SP>(m, s12, s13, B);
   } else {
     bw_basis(m, s12, s13, B);
   }
   Cplx<T> A = combine<NR>(m, sm, B);
-  const bool reim = SIG == 0 && m.reim;  // the specialised kernels serve magnitude/phase only
+  // the S-wave form: at run time, or fixed by a specialised kernel's signature
+  const bool reim = SIG == 0 ? m.reim != 0 : sig_reim(SIG);
   swave_add(m, sm, s12, reim, w.c12, A);
   swave_add(m, sm, s13, reim, w.c13, A);
   return A;
@@ -537,10 +545,10 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
     if constexpr (GRAD) {
       T v[16];
       if (ok) {
-        constexpr int NRg = SIG ? sig_count(SIG) : kMaxRes;
+        constexpr int NRg = sig_spins(SIG) ? sig_count(sig_spins(SIG)) : kMaxRes;
 #pragma unroll
         for (int r = 0; r < NRg; ++r) {
-          if (SIG || r < R) {
+          if (sig_spins(SIG) || r < R) {
             gc[2 * r] += T(2) * wt * (A.re * B[r].re + A.im * B[r].im);
             gc[2 * r + 1] += T(2) * wt * (A.im * B[r].re - A.re * B[r].im);
           }
@@ -558,7 +566,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
             }
           }
         }
-        const bool reim = SIG == 0 && m.reim != 0;
+        const bool reim = SIG == 0 ? m.reim != 0 : sig_reim(SIG);
         swave_adjoint(sm, sw.c12, reim, A, wt, v);
         swave_adjoint(sm, sw.c13, reim, A, wt, v + 8);
       } else {
@@ -781,21 +789,23 @@ static cudaError_t run_eval(const EvalArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// The model's compile-time signature, if a specialised FP32 kernel exists
-// (magnitude/phase S-wave only).
+// The model's compile-time signature, if a specialised FP32 kernel exists: a
+// P-wave and a D-wave, with either S-wave form.
 static int model_sig(const Model& m) {
-  if (!m.reim && m.n_res == 2 && m.cf.L[0] == 1 && m.cf.L[1] == 2) return kSigPD;
+  if (m.n_res == 2 && m.cf.L[0] == 1 && m.cf.L[1] == 2) return m.reim ? kSigPDReim : kSigPD;
   return 0;
 }
 
 template <typename T, typename EvT>
-static cudaError_t dispatch_eval(bool grad, bool cached, bool pd, const EvalArgs& a, int grid,
+static cudaError_t dispatch_eval(bool grad, bool cached, int sig, const EvalArgs& a, int grid,
                                  cudaStream_t st) {
   if (cached) return grad ? run_eval<T, EvT, true, 0, true>(a, grid, st)
                           : run_eval<T, EvT, false, 0, true>(a, grid, st);
   if constexpr (std::is_same<T, float>::value) {
-    if (pd) return grad ? run_eval<T, EvT, true, kSigPD>(a, grid, st)
-                        : run_eval<T, EvT, false, kSigPD>(a, grid, st);
+    if (sig == kSigPD) return grad ? run_eval<T, EvT, true, kSigPD>(a, grid, st)
+                                   : run_eval<T, EvT, false, kSigPD>(a, grid, st);
+    if (sig == kSigPDReim) return grad ? run_eval<T, EvT, true, kSigPDReim>(a, grid, st)
+                                       : run_eval<T, EvT, false, kSigPDReim>(a, grid, st);
   }
   return grad ? run_eval<T, EvT, true>(a, grid, st) : run_eval<T, EvT, false>(a, grid, st);
 }
@@ -803,7 +813,7 @@ static cudaError_t dispatch_eval(bool grad, bool cached, bool pd, const EvalArgs
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t st) {
   const bool cached = a.basis_norm != nullptr || a.basis_data != nullptr;
-  const bool pd = model_sig(a.model) == kSigPD;
+  const int pd = model_sig(a.model);
   if (compute_f32) {
     if (ev_f32) return dispatch_eval<float, float2>(grad, cached, pd, a, grid, st);
     return dispatch_eval<float, double2>(grad, cached, pd, a, grid, st);
@@ -873,7 +883,7 @@ int toys_blocks_per_sm(int compute_f32, int ev_f32) {
 
 cudaError_t launch_basis(int compute_f32, int ev_f32, const Model& m, const void* ev, int64_t n,
                          void* out, int grid, cudaStream_t st) {
-  const bool pd = model_sig(m) == kSigPD;
+  const bool pd = sig_spins(model_sig(m)) == kSigPD;
   if (compute_f32) {
     if (ev_f32) {
       if (pd) basis_kernel<float, float2, kSigPD><<<grid, kThreads, 0, st>>>(m, (const float2*)ev, n, (Cplx<float>*)out);
@@ -898,18 +908,20 @@ static int occ() {
 }
 
 template <typename T, typename EvT>
-static int occ_pair(bool cached, bool pd) {
+static int occ_pair(bool cached, int sig) {
   // blocks per SM of the variant that will run, the smaller of its NLL-only
   // and NLL+gradient kernels (both share one grid, so they sum identically)
   if (cached) return std::min(occ<T, EvT, false, 0, true>(), occ<T, EvT, true, 0, true>());
   if constexpr (std::is_same<T, float>::value) {
-    if (pd) return std::min(occ<T, EvT, false, kSigPD>(), occ<T, EvT, true, kSigPD>());
+    if (sig == kSigPD) return std::min(occ<T, EvT, false, kSigPD>(), occ<T, EvT, true, kSigPD>());
+    if (sig == kSigPDReim)
+      return std::min(occ<T, EvT, false, kSigPDReim>(), occ<T, EvT, true, kSigPDReim>());
   }
   return std::min(occ<T, EvT, false>(), occ<T, EvT, true>());
 }
 
 int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached) {
-  const bool pd = model_sig(m) == kSigPD;
+  const int pd = model_sig(m);
   if (compute_f32) return ev_f32 ? occ_pair<float, float2>(cached, pd)
                                  : occ_pair<float, double2>(cached, pd);
   return ev_f32 ? occ_pair<double, float2>(cached, pd) : occ_pair<double, double2>(cached, pd);
