@@ -174,12 +174,13 @@ int mipwa_set_swave_form(mipwa_ctx* ctx, int form);
  * one spline cell (j12, j13) each event's amplitude is b^T theta_cell with
  * the local basis b = (B_0..B_{R-1}, 1, t12, t12^2, t12^3, t13, t13^2,
  * t13^3), B_r the Bose-symmetrised Breit-Wigner terms and t = s - s_j, so the
- * context stores once, in FP64, the cell sums of conj(b) b^T: 22 + 14R + R^2
- * doubles per cell ((N-1)^2 cells). Every evaluation then takes the integral
+ * context stores once the cell sums of conj(b) b^T: 22 + 14R + R^2 doubles per
+ * cell ((N-1)^2 cells), FP64 products and sums, with B_r computed in the
+ * context's compute mode. Every evaluation then takes the integral
  * and its gradient from these moments and the current spline cubics, with
  * O(cells) work instead of O(N_norm) events; the value equals the direct sum
  * up to rounding. The moments are rebuilt on the first evaluation after
- * set_masses, set_model or set_norm_sample; mipwa_build_norm_gram builds them
+ * set_masses, set_model, set_resonances, set_norm_sample or set_compute_mode; mipwa_build_norm_gram builds them
  * at once (to time that cost apart). Evaluations return MIPWA_ESTATE while
  * the form is MIPWA_SWAVE_MAGPHASE, and MIPWA_EINVAL when the normalisation
  * sample holds 2^31 events or more. Batched toys (mipwa_nll_grad_toys) use

@@ -318,8 +318,8 @@ int build_gram(mipwa_ctx* c) {
   const int ev32 = smp.dtype == MIPWA_F32;
   CK(c, launch_cell_bounds(ev32, c->model.kn, smp.cur, smp.n, c->d_cells, c->d_cells + nkeys,
                            grid_for(c, smp.n), c->stream));
-  CK(c, launch_gram_build(ev32, c->model, smp.cur, c->d_cells, c->d_cells + nkeys, c->d_gram,
-                          c->stream));
+  CK(c, launch_gram_build(ev32, c->mode == MIPWA_F32, c->model, smp.cur, c->d_cells,
+                          c->d_cells + nkeys, c->d_gram, c->stream));
   c->launches += 2;
   CK(c, cudaStreamSynchronize(c->stream));
   c->gram_valid = true;
@@ -877,7 +877,10 @@ int mipwa_set_compute_mode(mipwa_ctx* c, int mode) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (mode != MIPWA_F64 && mode != MIPWA_F32) return fail(c, MIPWA_EINVAL, "bad compute mode");
-  if (mode != c->mode) invalidate_basis(c);
+  if (mode != c->mode) {
+    invalidate_basis(c);
+    c->gram_valid = false;  // the moments' Breit-Wigner terms follow the mode
+  }
   c->mode = mode;
   return MIPWA_OK;
 }

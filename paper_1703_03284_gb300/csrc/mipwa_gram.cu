@@ -10,11 +10,15 @@
 // normalisation sum over the cell's events is theta^H G theta with
 // G = sum conj(b) b^T, which the moments of gram_moments() hold.
 //
-//  * gram_build_kernel (once per model and sample, FP64): one block per cell
-//    sums the moments over the cell's events, which the set-time sort stored
+//  * gram_build_kernel (once per model and sample): one block per cell sums
+//    the moments over the cell's events, which the set-time sort stored
 //    contiguously. Threads first compute one event each (kinematics, B_r,
 //    powers of t) into shared memory, then one thread per moment sums its
 //    products over the tile in event order: the result is deterministic.
+//    Products and sums are FP64; B_r is FP64 for the FP64 compute mode and
+//    comes from the FP32-mixed form (bias-free, as the FP32 event kernels
+//    compute it) for the FP32 mode, which makes the build FP64-bound on the
+//    products only.
 //  * gram_rows_kernel (every evaluation, FP64): one block per j12 segment,
 //    one thread per j13; each cell's v = G theta gives its share of the
 //    integral (Re theta^H v) and of the gradient (2 v, mapped onto c_r and
@@ -25,6 +29,7 @@
 
 #include "mipwa_amp.cuh"
 #include "mipwa_kernels.cuh"
+#include "mipwa_pair.cuh"
 
 namespace mipwa {
 
@@ -104,7 +109,7 @@ __device__ void moment_desc(int idx, int R, int& i1, int& j1, int& i2, int& j2, 
   }
 }
 
-template <typename EvT>
+template <typename EvT, bool F32B>
 __global__ void __launch_bounds__(kGramThreads) gram_build_kernel(const Model m, const EvT* ev,
                                                                   const int* first,
                                                                   const int* last,
@@ -137,13 +142,25 @@ __global__ void __launch_bounds__(kGramThreads) gram_build_kernel(const Model m,
         v[k] = p1;
         v[6 + k] = p2;
       }
-      Cplx<double> B[kMaxRes];
-      bw_basis(m, s12, s13, B);
+      if constexpr (F32B) {
+        Cplx<float> B[kMaxRes];
+        bw_basis_pair(m, (float)e.x, (float)e.y, B);
 #pragma unroll
-      for (int r = 0; r < kMaxRes; ++r) {
-        if (r < R) {
-          v[13 + 2 * r] = B[r].re;
-          v[14 + 2 * r] = B[r].im;
+        for (int r = 0; r < kMaxRes; ++r) {
+          if (r < R) {
+            v[13 + 2 * r] = (double)B[r].re * m.cscale[r];
+            v[14 + 2 * r] = (double)B[r].im * m.cscale[r];
+          }
+        }
+      } else {
+        Cplx<double> B[kMaxRes];
+        bw_basis(m, s12, s13, B);
+#pragma unroll
+        for (int r = 0; r < kMaxRes; ++r) {
+          if (r < R) {
+            v[13 + 2 * r] = B[r].re;
+            v[14 + 2 * r] = B[r].im;
+          }
         }
       }
     }
@@ -296,15 +313,25 @@ __global__ void __launch_bounds__(64) gram_rows_kernel(const Model m, const doub
 
 }  // namespace
 
-cudaError_t launch_gram_build(int ev_f32, const Model& m, const void* ev, const int* first,
-                              const int* last, double* moments, cudaStream_t st) {
+cudaError_t launch_gram_build(int ev_f32, int compute_f32, const Model& m, const void* ev,
+                              const int* first, const int* last, double* moments,
+                              cudaStream_t st) {
   const int nkeys = (m.kn.n - 1) * (m.kn.n - 1);
-  if (ev_f32)
-    gram_build_kernel<float2><<<nkeys, kGramThreads, 0, st>>>(m, (const float2*)ev, first, last,
-                                                             moments);
-  else
-    gram_build_kernel<double2><<<nkeys, kGramThreads, 0, st>>>(m, (const double2*)ev, first,
-                                                              last, moments);
+  if (ev_f32) {
+    if (compute_f32)
+      gram_build_kernel<float2, true><<<nkeys, kGramThreads, 0, st>>>(m, (const float2*)ev, first,
+                                                                     last, moments);
+    else
+      gram_build_kernel<float2, false><<<nkeys, kGramThreads, 0, st>>>(m, (const float2*)ev, first,
+                                                                      last, moments);
+  } else {
+    if (compute_f32)
+      gram_build_kernel<double2, true><<<nkeys, kGramThreads, 0, st>>>(m, (const double2*)ev,
+                                                                      first, last, moments);
+    else
+      gram_build_kernel<double2, false><<<nkeys, kGramThreads, 0, st>>>(m, (const double2*)ev,
+                                                                       first, last, moments);
+  }
   return cudaGetLastError();
 }
 

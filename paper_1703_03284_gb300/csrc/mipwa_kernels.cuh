@@ -108,9 +108,11 @@ cudaError_t launch_cell_bounds(int ev_f32, const Knots& kn, const void* ev, int6
                                int* last, int grid, cudaStream_t stream);
 
 // Re/Im form: per-cell moments (gram_moments(R) doubles per cell, (N-1)^2
-// cells) of a sample grouped by cell, FP64.
-cudaError_t launch_gram_build(int ev_f32, const Model& m, const void* ev, const int* first,
-                              const int* last, double* moments, cudaStream_t stream);
+// cells) of a sample grouped by cell: FP64 products and sums; the
+// Breit-Wigner terms in FP64, or in the FP32-mixed form when compute_f32.
+cudaError_t launch_gram_build(int ev_f32, int compute_f32, const Model& m, const void* ev,
+                              const int* first, const int* last, double* moments,
+                              cudaStream_t stream);
 // Re/Im form: the normalisation rows of n_sets parameter sets (coefficients
 // at coef + set * coef_stride, prepare-kernel layout): set s writes rows
 // [s * row_stride, s * row_stride + N - 1) of `rows` in the partial-row layout

@@ -183,4 +183,23 @@ __device__ __forceinline__ CplxP bw_p(const ConstsF& c, int r, int L, const Chan
   return CplxP{mul2(f, drDR), mul2(f, G)};
 }
 
+// B_r / cscale_r of both channels summed (Bose symmetrisation), resonance
+// spins read from the model at run time.
+__device__ __forceinline__ void bw_basis_pair(const Model& m, float s12, float s13,
+                                              Cplx<float>* B) {
+  const ConstsF& c = m.cf;
+  const ChanP k = channel_p(c, P2{s12, s13});
+  F2P z1;
+  P2 z2;
+  zemach_p(c, k, P2{s13, s12}, z1, z2);
+#pragma unroll
+  for (int r = 0; r < kMaxRes; ++r) {
+    if (r < m.n_res) {
+      const CplxP u = bw_p(c, r, c.L[r], k, z1, z2);
+      B[r].re = u.re.x + u.re.y;
+      B[r].im = u.im.x + u.im.y;
+    }
+  }
+}
+
 }  // namespace mipwa
