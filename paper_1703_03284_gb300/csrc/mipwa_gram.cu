@@ -167,7 +167,11 @@ __global__ void __launch_bounds__(kGramThreads) gram_build_kernel(const Model m,
     __syncthreads();
     if ((int)threadIdx.x < M) {
       const int ne = e1 - base < kGramThreads ? e1 - base : kGramThreads;
-      for (int k = 0; k < ne; ++k) acc += V[k][i1] * V[k][j1] + s2 * (V[k][i2] * V[k][j2]);
+      if (s2 == 0.0) {  // one product: all moments but the |B|^2 and conj(B_r) B_s ones
+        for (int k = 0; k < ne; ++k) acc = fma(V[k][i1], V[k][j1], acc);
+      } else {
+        for (int k = 0; k < ne; ++k) acc = fma(V[k][i1], V[k][j1], fma(s2 * V[k][i2], V[k][j2], acc));
+      }
     }
     __syncthreads();
   }
