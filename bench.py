@@ -222,10 +222,42 @@ def cpu_baseline(spec, params, n: int = 200_000, target_s: float = 10.0):
     for _ in range(reps):
         o.nll_grad(params, data, norm, threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": reps * 2 * n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+    base = {"value": reps * 2 * n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
             "sample": f"{n} data + {n} normalisation events of the same model (float32-rounded, "
                       f"drawn with the oracle's density), {reps} NLL+grad evaluation(s), "
                       f"{cores} OpenMP threads"}
+    return base, accuracy_vs_oracle(spec, params, o, data, norm, cores)
+
+
+def accuracy_vs_oracle(spec, params, o, data, norm, cores):
+    """The error of each compute form of the library against the oracle on the
+    oracle's own sample (the events are float32 values, so every form sees the
+    same events)."""
+    import numpy as np
+    import torch
+
+    from paper_1703_03284_gb300 import F32, F64, Likelihood
+
+    vr, gr = o.nll_grad(params, data, norm, threads=cores)
+    a2r = o.amp2(params, norm)
+    out = {"n_data": len(data), "n_norm": len(norm), "oracle_nll": vr}
+    for mode, name in ((F64, "fp64"), (F32, "fp32_mixed")):
+        dt = torch.float32 if mode == F32 else torch.float64
+        d = torch.from_numpy(data).to("cuda", dt)
+        nm = torch.from_numpy(norm).to("cuda", dt)
+        lik = Likelihood(torch.cuda.current_device(), mode)
+        lik.set_spec(spec)
+        lik.set_events(d)
+        lik.set_norm_sample(nm)
+        v, g = lik.nll_grad(params)
+        a2 = lik.amp2(params, nm).cpu().numpy()
+        rel = np.abs(a2 / a2r - 1.0)
+        out[name] = {"nll_abs_err": abs(v - vr), "nll_rel_err": abs(v - vr) / abs(vr),
+                     "grad_rel_err": float(np.linalg.norm(g - gr) / np.linalg.norm(gr)),
+                     "amp2_rel_err_median": float(np.median(rel)),
+                     "amp2_rel_err_max": float(rel.max()),
+                     "amp2_frac_above_1e-5": float(np.mean(rel > 1e-5))}
+    return out
 
 
 def run_reference(args, world, rank):
@@ -394,13 +426,17 @@ def reim_leg(args, lik, spec, params, events, stream, world):
     lik.enable_norm_gram(True)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("reim_moments_build")
     a.record(stream)
     lik.build_norm_gram()
     b.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     out["moments_build_ms"] = a.elapsed_time(b)
     out["moments_doubles"] = (spec.n_knots - 1) ** 2 * (22 + 14 * spec.n_res + spec.n_res ** 2)
+    torch.cuda.nvtx.range_push("reim_moments")
     out["fp32_moments"] = timed(args.reim_steps)
+    torch.cuda.nvtx.range_pop()
     lik.set_compute_mode(F64)
     out["fp64_moments"] = timed(max(1, args.fp64_steps))
     lik.set_compute_mode(F32)
@@ -642,9 +678,9 @@ def run(args, world, rank, local, stream):
 
     paper = paper_fit_leg(rank) if args.paper_fit else None
 
-    cpu = None
+    cpu, accuracy = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(spec, params)
+        cpu, accuracy = cpu_baseline(spec, params)
 
     if rank == 0:
         print(json.dumps({
@@ -658,7 +694,7 @@ def run(args, world, rank, local, stream):
             "roofline": roofline, "fp64_plain": fp64, "fp32_cached_basis": cached,
             "batched_toys": toys, "reim_moment_normalisation": reim,
             "paper_workload_fit": paper, "e2e": e2e,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy,
             "gpu_launches": launches, "clocks": clk,
         }), flush=True)
 
