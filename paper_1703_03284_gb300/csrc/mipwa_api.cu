@@ -60,6 +60,8 @@ struct mipwa_ctx {
   // overlaps the previous sample's sort on the context stream
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done = nullptr;
+  static constexpr int kCopyPieces = 4;  // a sorted sample arrives in pieces, each counted on arrival
+  cudaEvent_t piece_done[kCopyPieces] = {};
   bool basis_on = false;
   // Re/Im form: normalisation from per-cell moments of the normalisation sample
   bool gram_on = false;
@@ -368,27 +370,45 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
       if (!is_device_ptr(ptr))
         return fail(c, MIPWA_EINVAL, "on_device set but the pointer is not device memory");
       CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
-    } else {
-      // on the copy stream, after the last kernel that used this sample's
-      // spare buffer, so that it overlaps other work still running on the
-      // context stream (another sample's sort); the context stream waits for it
-      CK(c, cudaStreamWaitEvent(c->copy_stream, smp.spare_free, 0));
-      CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyHostToDevice, c->copy_stream));
-      CK(c, cudaEventRecord(c->copy_done, c->copy_stream));
-      CK(c, cudaStreamWaitEvent(c->stream, c->copy_done, 0));
     }
     CK(c, cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream));
     if (will_sort) {
-      // the first counting pass of the sort also counts the outside events
       rc = ensure_sortwork(c);
       if (rc) return rc;
+    }
+    if (!on_device) {
+      // on the copy stream, after the last kernel that used this sample's
+      // spare buffer, so that it overlaps other work still running on the
+      // context stream (another sample's sort); the context stream waits for
+      // each piece and, for a sorted sample, counts it (the first counting
+      // pass of the sort, which also counts the outside events) while the
+      // next piece is in flight
+      CK(c, cudaStreamWaitEvent(c->copy_stream, smp.spare_free, 0));
+      const int pieces = will_sort ? mipwa_ctx::kCopyPieces : 1;
+      const size_t eb = ev_bytes(dtype);
+      for (int p = 0; p < pieces; ++p) {
+        const int64_t e0 = will_sort ? sort_piece_begin(n, p, pieces) : 0;
+        const int64_t e1 = will_sort ? sort_piece_begin(n, p + 1, pieces) : n;
+        if (e1 > e0)
+          CK(c, cudaMemcpyAsync((char*)smp.spare + e0 * eb, (const char*)ptr + e0 * eb,
+                                (e1 - e0) * eb, cudaMemcpyHostToDevice, c->copy_stream));
+        CK(c, cudaEventRecord(c->piece_done[p], c->copy_stream));
+        CK(c, cudaStreamWaitEvent(c->stream, c->piece_done[p], 0));
+        if (will_sort)
+          CK(c, launch_sort_count_checked(dtype == MIPWA_F32, c->model, smp.spare, n,
+                                          c->d_sortwork, c->d_count, c->stream, p, pieces));
+      }
+      c->launches += will_sort ? pieces : 0;
+    } else if (will_sort) {
       CK(c, launch_sort_count_checked(dtype == MIPWA_F32, c->model, smp.spare, n,
                                       c->d_sortwork, c->d_count, c->stream));
-    } else {
+      c->launches++;
+    }
+    if (!will_sort) {
       CK(c, launch_inside(dtype == MIPWA_F32, c->model, smp.spare, n, nullptr, c->d_count,
                           grid_for(c, n), c->stream));
+      c->launches++;
     }
-    c->launches++;
     CK(c, cudaMemcpyAsync(&outside, c->d_count, sizeof(outside), cudaMemcpyDeviceToHost,
                           c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -823,6 +843,9 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
   if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming) != cudaSuccess)
     return bail(MIPWA_ECUDA);
+  for (cudaEvent_t& e : c->piece_done)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return bail(MIPWA_ECUDA);
   for (mipwa_ctx::Sample* smp : {&c->data, &c->norm, &c->toys}) {
     if (cudaEventCreateWithFlags(&smp->spare_free, cudaEventDisableTiming) != cudaSuccess)
       return bail(MIPWA_ECUDA);
@@ -859,6 +882,8 @@ void mipwa_destroy(mipwa_ctx* c) {
   for (mipwa_ctx::Sample* smp : {&c->data, &c->norm, &c->toys})
     if (smp->spare_free) cudaEventDestroy(smp->spare_free);
   if (c->copy_done) cudaEventDestroy(c->copy_done);
+  for (cudaEvent_t e : c->piece_done)
+    if (e) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;

@@ -96,10 +96,13 @@ cudaError_t launch_sort(int ev_f32, const Model& m, const void* src, int64_t n, 
                         void* dst, int* work, cudaStream_t stream);
 // The same split at the first count, which also adds the number of events
 // outside the Dalitz plot to *outside (device): validate, then finish with
-// launch_sort_rest (nothing is written before it).
+// launch_sort_rest (nothing is written before it). The count may run in
+// n_pieces (a power of two up to 64) launches, piece p reading only the events
+// [sort_piece_begin(n, p, n_pieces), sort_piece_begin(n, p + 1, n_pieces)).
 cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* src, int64_t n,
                                       int* work, unsigned long long* outside,
-                                      cudaStream_t stream);
+                                      cudaStream_t stream, int piece = 0, int n_pieces = 1);
+int64_t sort_piece_begin(int64_t n, int piece, int n_pieces);
 cudaError_t launch_sort_rest(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
                              void* dst, int* work, cudaStream_t stream);
 // Index range [first[k], last[k]) of every spline cell k = j12 (N-1) + j13 in

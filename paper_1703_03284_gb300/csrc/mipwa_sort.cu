@@ -77,12 +77,13 @@ __host__ __device__ inline int64_t chunk_begin(int64_t n, int b) {
 // keys are clamped segments, so the histogram stays in range).
 template <typename EvT, bool FULL, bool CHECK>
 __global__ void __launch_bounds__(32 * kSortWarps)
-    sort_count_kernel(const Model m, const EvT* ev, int64_t n,
+    sort_count_kernel(const Model m, const EvT* ev, int64_t n, int chunk0,
                       int* counts /* [kSortBlocks][nkeys] */, unsigned long long* outside) {
   extern __shared__ int hist_all[];
   const Knots& kn = m.kn;
   const int nkeys = pass_keys<FULL>(kn.n);
-  const int lane = threadIdx.x & 31, chunk = blockIdx.x * kSortWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int chunk = chunk0 + blockIdx.x * kSortWarps + (threadIdx.x >> 5);
   int* hist = hist_all + (threadIdx.x >> 5) * nkeys;
   for (int k = lane; k < nkeys; k += 32) hist[k] = 0;
   __syncwarp();
@@ -249,14 +250,16 @@ cudaError_t sort_workspace_ints(int n_knots, size_t* ints) {
   return cudaSuccess;
 }
 
+// Count the chunks [c0, c1) (multiples of kSortWarps).
 template <typename EvT, bool FULL, bool CHECK>
 static cudaError_t count_pass(const Model& m, const EvT* src, int64_t n, int* work,
-                              unsigned long long* outside, cudaStream_t st) {
+                              unsigned long long* outside, cudaStream_t st, int c0 = 0,
+                              int c1 = kSortBlocks) {
   const size_t smem = (size_t)kSortWarps * pass_keys<FULL>(m.kn.n) * sizeof(int);
   auto kern = sort_count_kernel<EvT, FULL, CHECK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<kSortBlocks / kSortWarps, 32 * kSortWarps, smem, st>>>(m, src, n, work, outside);
+  kern<<<(c1 - c0) / kSortWarps, 32 * kSortWarps, smem, st>>>(m, src, n, c0, work, outside);
   return cudaGetLastError();
 }
 
@@ -292,9 +295,16 @@ static cudaError_t sort_rest(const Model& m, const EvT* src, int64_t n, EvT* tmp
 }
 
 cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* src, int64_t n,
-                                      int* work, unsigned long long* outside, cudaStream_t st) {
-  if (ev_f32) return count_pass<float2, false, true>(m, (const float2*)src, n, work, outside, st);
-  return count_pass<double2, false, true>(m, (const double2*)src, n, work, outside, st);
+                                      int* work, unsigned long long* outside, cudaStream_t st,
+                                      int piece, int n_pieces) {
+  const int c0 = kSortBlocks / n_pieces * piece, c1 = kSortBlocks / n_pieces * (piece + 1);
+  if (ev_f32)
+    return count_pass<float2, false, true>(m, (const float2*)src, n, work, outside, st, c0, c1);
+  return count_pass<double2, false, true>(m, (const double2*)src, n, work, outside, st, c0, c1);
+}
+
+int64_t sort_piece_begin(int64_t n, int piece, int n_pieces) {
+  return chunk_begin(n, kSortBlocks / n_pieces * piece);
 }
 
 cudaError_t launch_sort_rest(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
