@@ -62,12 +62,6 @@ struct mipwa_ctx {
   cudaEvent_t copy_done = nullptr;
   static constexpr int kCopyPieces = 4;  // a sorted sample arrives in pieces, each counted on arrival
   cudaEvent_t piece_done[kCopyPieces] = {};
-  // a sample whose sort is still queued on the context stream (set_* returned
-  // without waiting for it): the next evaluation runs the other sample's half
-  // on aux_stream, overlapping that sort
-  Sample* pending = nullptr;
-  cudaStream_t aux_stream = nullptr;
-  cudaEvent_t aux_prep = nullptr, aux_done = nullptr;
   bool basis_on = false;
   // Re/Im form: normalisation from per-cell moments of the normalisation sample
   bool gram_on = false;
@@ -436,7 +430,6 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
     // no wait: later work on the context stream is ordered after the sort, and
     // the next copy into this sample's spare buffer waits for this event
     CK(c, cudaEventRecord(smp.spare_free, c->stream));
-    c->pending = &smp;
     std::swap(smp.cur, smp.spare);
     std::swap(smp.cur_cap, smp.spare_cap);
     smp.sorted = true;
@@ -531,20 +524,11 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
     rc = build_gram(c);
     if (rc) return rc;
   }
-  // Split evaluation: while one sample's sort is still queued on the context
-  // stream, the other sample's blocks (and the spline setup) run on the aux
-  // stream once that sample is ready; the two launches share one finishing
-  // ticket, so whichever ends last reduces the rows.
-  mipwa_ctx::Sample* pend = c->pending;
-  c->pending = nullptr;
-  const bool split = pend && !gram && !c->basis_on && c->data.n > 0;
-  mipwa_ctx::Sample* early = split ? (pend == &c->norm ? &c->data : &c->norm) : nullptr;
-  cudaStream_t sp = split ? c->aux_stream : c->stream;  // stream of the setup
-  if (split) CK(c, cudaStreamWaitEvent(sp, early->spare_free, 0));
   std::memcpy(c->h_stage, params, P * sizeof(double));
-  CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, P * sizeof(double), cudaMemcpyHostToDevice, sp));
-  CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), sp));
-  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->d_coef32, sp);
+  CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, P * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
+  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->d_coef32, c->stream);
   CK(c, cudaGetLastError());
   EvalArgs a;
   a.data = c->data.cur;
@@ -564,32 +548,15 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   a.basis_data = c->basis_on ? c->data.basis : nullptr;
   a.basis_norm = (c->basis_on && !gram) ? c->norm.basis : nullptr;
   a.model = c->model;
-  if (c->timing) CK(c, cudaEventRecord(c->ev0, sp));
+  if (c->timing) CK(c, cudaEventRecord(c->ev0, c->stream));
   if (gram) {
     CK(c, launch_gram_rows(want_grad, f32, c->model, c->d_coef, 0, c->d_gram,
                            c->d_partials + (size_t)nb_d * W, nseg, 1, c->stream));
     c->launches++;
   }
-  if (split) {
-    // data blocks are global blocks [0, nb_d), normalisation blocks [nb_d, grid)
-    a.n_blocks = grid;
-    EvalArgs ea = a, pa = a;
-    const bool data_early = early == &c->data;
-    ea.block0 = data_early ? 0 : nb_d;
-    pa.block0 = data_early ? nb_d : 0;
-    const int eg = data_early ? nb_d : nb_n, pg = grid - eg;
-    CK(c, cudaEventRecord(c->aux_prep, sp));
-    CK(c, launch_eval(f32, ev32, want_grad, ea, eg, sp));
-    CK(c, cudaEventRecord(c->aux_done, sp));
-    CK(c, cudaStreamWaitEvent(c->stream, c->aux_prep, 0));
-    CK(c, launch_eval(f32, ev32, want_grad, pa, pg, c->stream));
-    CK(c, cudaStreamWaitEvent(c->stream, c->aux_done, 0));
-    c->launches += 3;
-  } else {
-    CK(c, launch_eval(f32, ev32, want_grad, a, grid, c->stream));
-    c->launches += 2;
-  }
+  CK(c, launch_eval(f32, ev32, want_grad, a, grid, c->stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, c->stream));
+  c->launches += 2;
   double* h_out = c->h_stage + kStage / 2;
   int* h_flags = (int*)(h_out + 1 + P);
   CK(c, cudaMemcpyAsync(h_out, c->d_out, (1 + (want_grad ? P : 0)) * sizeof(double),
@@ -879,10 +846,6 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
   for (cudaEvent_t& e : c->piece_done)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
       return bail(MIPWA_ECUDA);
-  if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->aux_prep, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->aux_done, cudaEventDisableTiming) != cudaSuccess)
-    return bail(MIPWA_ECUDA);
   for (mipwa_ctx::Sample* smp : {&c->data, &c->norm, &c->toys}) {
     if (cudaEventCreateWithFlags(&smp->spare_free, cudaEventDisableTiming) != cudaSuccess)
       return bail(MIPWA_ECUDA);
@@ -897,7 +860,6 @@ void mipwa_destroy(mipwa_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
-  if (c->aux_stream) cudaStreamSynchronize(c->aux_stream);
   for (void* p : {(void*)c->d_lu, (void*)c->d_params, (void*)c->d_coef, (void*)c->d_coef32,
                   (void*)c->d_out,
                   (void*)c->d_flags, (void*)c->d_counter, (void*)c->d_count,
@@ -922,9 +884,6 @@ void mipwa_destroy(mipwa_ctx* c) {
   if (c->copy_done) cudaEventDestroy(c->copy_done);
   for (cudaEvent_t e : c->piece_done)
     if (e) cudaEventDestroy(e);
-  if (c->aux_prep) cudaEventDestroy(c->aux_prep);
-  if (c->aux_done) cudaEventDestroy(c->aux_done);
-  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;

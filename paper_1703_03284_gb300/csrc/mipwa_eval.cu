@@ -649,11 +649,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
   __shared__ EvalSmem<T> sm;
   const Model& m = a.model;
   stage(sm, m, EvalCoefs{a.coef, a.coef32});
-  const int g = a.block0 + (int)blockIdx.x;  // global block of a split evaluation
-  const bool is_data = g < a.nb_data;
+  const bool is_data = (int)blockIdx.x < a.nb_data;
   const int64_t n = is_data ? a.n_data : a.n_norm;
   const int nb = is_data ? a.nb_data : a.nb_norm;
-  const int b = is_data ? g : g - a.nb_data;
+  const int b = is_data ? (int)blockIdx.x : (int)blockIdx.x - a.nb_data;
   const EvT* ev = reinterpret_cast<const EvT*>(is_data ? a.data : a.norm);
   const Cplx<T>* cached =
       reinterpret_cast<const Cplx<T>*>(is_data ? a.basis_data : a.basis_norm);
@@ -665,14 +664,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
   const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
   accumulate_range<T, EvT, GRAD, SIG, CACHED, BWG>(sm, m, ev, cached, n, c0, c1,
                                                    (int64_t)kThreads, is_data,
-                                                   a.partials + (size_t)g * W, a.flags,
+                                                   a.partials + (size_t)blockIdx.x * W, a.flags,
                                                    a.coef);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int ticket = atomicAdd(a.counter, 1u);
-    const unsigned int blocks = a.n_blocks > 0 ? (unsigned int)a.n_blocks : gridDim.x;
-    sm.is_last = ticket == blocks - 1;
+    sm.is_last = ticket == gridDim.x - 1;
   }
   __syncthreads();
   if (!sm.is_last) return;

@@ -28,12 +28,6 @@ struct EvalArgs {
   const void* basis_data;    // cached B_r per data event (resonance-major) or null
   const void* basis_norm;    // the same for the normalisation sample; null: compute B_r
   Model model;
-  // An evaluation may be split into launches (on different streams): this
-  // launch's blocks are global blocks block0 .. block0 + gridDim.x - 1 of
-  // n_blocks in all (0: one launch, n_blocks = gridDim.x); the last block of
-  // any launch to finish reduces the rows.
-  int block0 = 0;
-  int n_blocks = 0;
 };
 
 enum { kFlagData = 1, kFlagNorm = 2, kFlagIntegral = 4 };
