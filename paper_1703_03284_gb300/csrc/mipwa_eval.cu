@@ -799,6 +799,13 @@ static int model_sig(const Model& m) {
 template <typename T, typename EvT>
 static cudaError_t dispatch_eval(bool grad, bool cached, int sig, const EvalArgs& a, int grid,
                                  cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (cached && sig == kSigPD) return grad ? run_eval<T, EvT, true, kSigPD, true>(a, grid, st)
+                                             : run_eval<T, EvT, false, kSigPD, true>(a, grid, st);
+    if (cached && sig == kSigPDReim)
+      return grad ? run_eval<T, EvT, true, kSigPDReim, true>(a, grid, st)
+                  : run_eval<T, EvT, false, kSigPDReim, true>(a, grid, st);
+  }
   if (cached) return grad ? run_eval<T, EvT, true, 0, true>(a, grid, st)
                           : run_eval<T, EvT, false, 0, true>(a, grid, st);
   if constexpr (std::is_same<T, float>::value) {
@@ -911,6 +918,12 @@ template <typename T, typename EvT>
 static int occ_pair(bool cached, int sig) {
   // blocks per SM of the variant that will run, the smaller of its NLL-only
   // and NLL+gradient kernels (both share one grid, so they sum identically)
+  if constexpr (std::is_same<T, float>::value) {
+    if (cached && sig == kSigPD)
+      return std::min(occ<T, EvT, false, kSigPD, true>(), occ<T, EvT, true, kSigPD, true>());
+    if (cached && sig == kSigPDReim)
+      return std::min(occ<T, EvT, false, kSigPDReim, true>(), occ<T, EvT, true, kSigPDReim, true>());
+  }
   if (cached) return std::min(occ<T, EvT, false, 0, true>(), occ<T, EvT, true, 0, true>());
   if constexpr (std::is_same<T, float>::value) {
     if (sig == kSigPD) return std::min(occ<T, EvT, false, kSigPD>(), occ<T, EvT, true, kSigPD>());
