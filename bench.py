@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--n-events", type=int, default=100_000_000,
                     help="data events (= normalisation events)")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--nll-steps", type=int, default=50, help="NLL-only (no gradient) steps")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cached-steps", type=int, default=10)
     ap.add_argument("--toys-steps", type=int, default=3)
@@ -573,6 +574,21 @@ def run(args, world, rank, local, stream):
                 "kernel_ms": kms / kn,
                 "peak_note": "FP32 from unit counts x 2070 MHz (nominal, not measured)"}
 
+    # ---- NLL alone (no gradient), FP32-mixed, same events
+    nll_only = None
+    if args.nll_steps > 0:
+        lik.nll(params)
+        torch.cuda.synchronize()
+        n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0.record(stream)
+        for _ in range(args.nll_steps):
+            lik.nll(params)
+        n1.record(stream)
+        torch.cuda.synchronize()
+        tn = max_over_ranks(n0.elapsed_time(n1), world) / args.nll_steps
+        nll_only = {"fp32": {"ms_per_step": tn, "value": world * events / (tn / 1e3),
+                             "unit": "events/s"}}
+
     # ---- plain FP64 on the same events
     fp64 = None
     if args.fp64_steps > 0:
@@ -598,6 +614,15 @@ def run(args, world, rank, local, stream):
         f1.record(stream)
         torch.cuda.synchronize()
         tbw = max_over_ranks(f0.elapsed_time(f1), world) / args.fp64_steps
+        if nll_only is not None:
+            f0.record(stream)
+            for _ in range(args.fp64_steps):
+                lik.nll(params)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            tn64 = max_over_ranks(f0.elapsed_time(f1), world) / args.fp64_steps
+            nll_only["fp64"] = {"ms_per_step": tn64, "value": world * events / (tn64 / 1e3),
+                                "unit": "events/s"}
         lik.set_compute_mode(F32)
         ach64 = FLOPS_PER_EVENT_GRAD * events / (kms64 / kn64 / 1e3) / 1e12
         fp64 = {"value": world * events * args.fp64_steps / (t64 / 1e3), "unit": "events/s",
@@ -691,7 +716,8 @@ def run(args, world, rank, local, stream):
             "config": {"workload": WORKLOAD, "n_data": n, "n_norm": n,
                        "l2": "inputs (1.6 GB) larger than L2 (129 MB); no flush needed",
                        "parallelism": f"replicas x{world} (no collective)"},
-            "roofline": roofline, "fp64_plain": fp64, "fp32_cached_basis": cached,
+            "roofline": roofline, "nll_only": nll_only, "fp64_plain": fp64,
+            "fp32_cached_basis": cached,
             "batched_toys": toys, "reim_moment_normalisation": reim,
             "paper_workload_fit": paper, "e2e": e2e,
             "cpu_baseline": cpu, "accuracy_vs_oracle": accuracy,
