@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
 // normalisation sample for one toy, and writes one partial row. Items come
 // chunk-major (all toys of a normalisation chunk in turn), so a chunk is read
 // from HBM once and then from L2.
-template <typename T, typename EvT, bool CACHED>
+template <typename T, typename EvT, bool CACHED, int SIG = 0>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) toys_kernel(const ToyArgs a) {
   __shared__ EvalSmem<T> sm;
   __shared__ int item_sh;
@@ -705,10 +705,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) toys_kernel(
     const Cplx<T>* cached =
         reinterpret_cast<const Cplx<T>*>(it.is_data ? a.basis_data : a.basis_norm);
     const int64_t n = it.is_data ? a.n_data : a.n_norm;
-    accumulate_range<T, EvT, true, 0, CACHED>(sm, m, ev, cached, n, it.start, it.end,
-                                              (int64_t)kThreads, it.is_data != 0,
-                                              a.partials + (size_t)it.row * W, a.flags,
-                                              a.coef + (size_t)it.toy * cs);
+    accumulate_range<T, EvT, true, SIG, CACHED>(sm, m, ev, cached, n, it.start, it.end,
+                                                (int64_t)kThreads, it.is_data != 0,
+                                                a.partials + (size_t)it.row * W, a.flags,
+                                                a.coef + (size_t)it.toy * cs);
   }
 }
 
@@ -831,8 +831,22 @@ cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& 
 
 template <typename T, typename EvT>
 static cudaError_t run_toys(bool cached, const ToyArgs& a, int grid, cudaStream_t st) {
-  if (cached) toys_kernel<T, EvT, true><<<grid, kThreads, 0, st>>>(a);
-  else toys_kernel<T, EvT, false><<<grid, kThreads, 0, st>>>(a);
+  // FP32 with the cached basis: kernels specialised for P+D models
+  const int sig = cached ? model_sig(a.model) : 0;
+  bool done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (sig == kSigPD) {
+      toys_kernel<T, EvT, true, kSigPD><<<grid, kThreads, 0, st>>>(a);
+      done = true;
+    } else if (sig == kSigPDReim) {
+      toys_kernel<T, EvT, true, kSigPDReim><<<grid, kThreads, 0, st>>>(a);
+      done = true;
+    }
+  }
+  if (!done) {
+    if (cached) toys_kernel<T, EvT, true><<<grid, kThreads, 0, st>>>(a);
+    else toys_kernel<T, EvT, false><<<grid, kThreads, 0, st>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   toys_finalize_kernel<T><<<a.n_toys, kThreads, 0, st>>>(a);
