@@ -59,7 +59,6 @@ struct mipwa_ctx {
   // host-to-device copies of new samples run here, so that one sample's copy
   // overlaps the previous sample's sort on the context stream
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t copy_done = nullptr;
   static constexpr int kCopyPieces = 4;  // a sorted sample arrives in pieces, each counted on arrival
   cudaEvent_t piece_done[kCopyPieces] = {};
   bool basis_on = false;
@@ -840,8 +839,7 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
   if (cudaMemset(c->d_counter, 0, sizeof(unsigned int)) != cudaSuccess) return bail(MIPWA_ECUDA);
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
     return bail(MIPWA_ECUDA);
-  if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(MIPWA_ECUDA);
   for (cudaEvent_t& e : c->piece_done)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
@@ -881,7 +879,6 @@ void mipwa_destroy(mipwa_ctx* c) {
   if (c->ev1) cudaEventDestroy(c->ev1);
   for (mipwa_ctx::Sample* smp : {&c->data, &c->norm, &c->toys})
     if (smp->spare_free) cudaEventDestroy(smp->spare_free);
-  if (c->copy_done) cudaEventDestroy(c->copy_done);
   for (cudaEvent_t e : c->piece_done)
     if (e) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
