@@ -363,3 +363,50 @@ def test_basis_cache(mode):
     lik.enable_basis_cache(False)
     v4, g4 = lik.nll_grad(p)
     check(v4, g4, mode)
+
+
+# ------------------------------------------ FP32-mixed form on other models
+def _fp32_vs_oracle(spec, o, data, norm, params_list, nll_tol=1e-2, grad_tol=2e-5):
+    d32, n32 = data.astype(np.float32), norm.astype(np.float32)
+    lik = Likelihood(0, F32)
+    lik.set_spec(spec)
+    lik.set_events(torch.from_numpy(d32).to(DEV))
+    lik.set_norm_sample(torch.from_numpy(n32).to(DEV))
+    for p in params_list:
+        v, g = lik.nll_grad(p)
+        vr, gr = o.nll_grad(p, d32.astype(np.float64), n32.astype(np.float64))
+        assert abs(v - vr) < nll_tol, (v, vr)
+        assert grad_rel(g, gr) < grad_tol
+
+
+def test_fp32_narrow_phi_kkk():
+    """K K K with the narrow phi(1020) (4 MeV): the FP32 form keeps m_r^2 - s
+    exact near the pole, so the NLL stays within tolerance at 10^6 events."""
+    name = "kkk_n40"
+    spec = P.spec_by_name(name)
+    data = P.data_sample(name, 1_000_000, f32=True)
+    norm = P.uniform_sample(name, 1_000_000, f32=True)
+    # a sizeable share of the events sits within a few widths of the pole
+    near = np.abs(np.minimum(data[:, 0], data[:, 1]) - 1.019461 ** 2) < 0.02
+    assert near.mean() > 0.05
+    _fp32_vs_oracle(spec, P.oracle_for(name), data, norm,
+                    [synth.true_params(spec), synth.perturbed_params(spec, 8, 0.02)])
+
+
+def test_fp32_nonuniform_knots_three_resonances():
+    """Non-uniform knots (segment search instead of the uniform index) and three
+    resonances including a scalar one: the generic FP32 kernel."""
+    spec = synth.ModelSpec(name="custom32", mD=synth.M_D, m1=synth.M_PI, m2=synth.M_PI,
+                           resonances=((0.77526, 0.1491, 1), (0.98, 0.06, 0), (1.2755, 0.1867, 2)),
+                           knots=(0.078, 0.2, 0.45, 0.8, 0.95, 1.3, 1.9, 2.5, 2.987))
+    import oracle
+    o = oracle.Oracle(spec)
+    rng = np.random.default_rng(2)
+    truth = np.concatenate([[0.2, 0.0, 0.1, 0.3, 0.3, -0.1], 1 + 0.3 * rng.random(9),
+                            np.linspace(0, 2.5, 9)])
+    dens = synth.numpy_density(lambda x: o.density(truth, x))
+    ins = synth.numpy_density(lambda x: o.inside(x).astype(np.float64))
+    data = synth.accept_reject(spec, 300_000, dens, seed=6, dtype=torch.float32).numpy()
+    norm = synth.uniform_in_plot(spec, 300_000, ins, seed=7, dtype=torch.float32).numpy()
+    p2 = truth + 0.02 * np.random.default_rng(3).standard_normal(truth.shape)
+    _fp32_vs_oracle(spec, o, data.astype(np.float64), norm.astype(np.float64), [truth, p2])
