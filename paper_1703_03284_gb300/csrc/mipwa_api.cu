@@ -110,7 +110,11 @@ struct mipwa_ctx {
 
 namespace {
 
-constexpr int kStage = 2 * (2 * kMaxRes + 2 * kMaxKnots + 8);
+// Pinned staging buffer of one evaluation (doubles): the parameters, then the
+// results [NLL, gradient (P), resonance derivatives (2R)], then the flags.
+constexpr int kParamsMax = 2 * kMaxRes + 2 * kMaxKnots;
+constexpr int kOutMax = 1 + kParamsMax + 2 * kMaxRes;
+constexpr int kStage = kParamsMax + kOutMax + 1;
 
 int fail(mipwa_ctx* c, int code, const char* fmt, ...) {
   if (c) {
@@ -556,7 +560,7 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   CK(c, launch_eval(f32, ev32, want_grad, a, grid, c->stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, c->stream));
   c->launches += 2;
-  double* h_out = c->h_stage + kStage / 2;
+  double* h_out = c->h_stage + kParamsMax;
   int* h_flags = (int*)(h_out + 1 + P);
   CK(c, cudaMemcpyAsync(h_out, c->d_out, (1 + (want_grad ? P : 0)) * sizeof(double),
                         cudaMemcpyDeviceToHost, c->stream));
@@ -636,7 +640,7 @@ int evaluate_bw(mipwa_ctx* c, const double* params, double* nll, double* grad,
   a.model = c->model;
   CK(c, launch_eval_bw(ev32, a, grid, c->stream));
   c->launches += 2;
-  double* h_out = c->h_stage + kStage / 2;
+  double* h_out = c->h_stage + kParamsMax;
   int* h_flags = (int*)(h_out + 1 + P + 2 * R);
   CK(c, cudaMemcpyAsync(h_out, c->d_out, (1 + P + 2 * R) * sizeof(double),
                         cudaMemcpyDeviceToHost, c->stream));
@@ -830,7 +834,7 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
       cudaMalloc(&c->d_params, P * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_coef, coef_size(kMaxKnots, kMaxRes) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_coef32, coef32_size(kMaxKnots, kMaxRes) * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&c->d_out, (1 + P) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_out, kOutMax * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_counter, sizeof(unsigned int)) != cudaSuccess ||
       cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
