@@ -10,7 +10,7 @@
 namespace mipwa {
 
 constexpr int kThreads = 256;        // threads per block of the event kernels
-constexpr int kFlushIters = 32;      // FP32 form: grid-stride iterations between bin flushes
+constexpr int kFlushIters = 64;      // FP32 form: grid-stride iterations between bin flushes
 
 struct EvalArgs {
   const void* data;   // n_data pairs (s12, s13)
