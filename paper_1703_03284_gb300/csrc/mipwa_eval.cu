@@ -85,7 +85,7 @@ struct EvalSmem<double> : SmemCommon {
 };
 template <>
 struct EvalSmem<float> : SmemCommon {
-  __align__(16) float coef[kMaxSeg * 16];  // hi/lo cubics about float(s_j)
+  __align__(16) float coef[kMaxSeg * kSeg32];  // hi/lo cubics about float(s_j), e^{i phi_ref}
   float knot[kMaxKnots];     // float(s_j)
   float knot_lo[kMaxKnots];  // s_j - float(s_j)
   float cre[kMaxRes], cre_lo[kMaxRes], cim[kMaxRes], cim_lo[kMaxRes];
@@ -108,14 +108,14 @@ __device__ void stage(EvalSmem<double>& sm, const Model& m, const EvalCoefs& cf)
 
 __device__ void stage(EvalSmem<float>& sm, const Model& m, const EvalCoefs& cf) {
   const int nseg = m.kn.n - 1;
-  for (int i = threadIdx.x; i < nseg * 16; i += blockDim.x) sm.coef[i] = cf.coef32[i];
+  for (int i = threadIdx.x; i < nseg * kSeg32; i += blockDim.x) sm.coef[i] = cf.coef32[i];
   for (int i = threadIdx.x; i < m.kn.n; i += blockDim.x) {
     const float hi = (float)m.kn.s[i];
     sm.knot[i] = hi;
     sm.knot_lo[i] = (float)(m.kn.s[i] - (double)hi);
   }
   if (threadIdx.x < m.n_res) {
-    const float* c = cf.coef32 + nseg * 16 + 4 * threadIdx.x;
+    const float* c = cf.coef32 + nseg * kSeg32 + 4 * threadIdx.x;
     sm.cre[threadIdx.x] = c[0];
     sm.cre_lo[threadIdx.x] = c[1];
     sm.cim[threadIdx.x] = c[2];
@@ -220,19 +220,47 @@ __device__ __forceinline__ Cplx<float> combine(const Model& m, const EvalSmem<fl
   return A;
 }
 
+// sin and cos of a small phase |d| <= kSmallPhase: Taylor series through d^9
+// and d^8 (truncation below 5e-12 there), the leading coefficients -1/6 and
+// 1/24 as float pairs (the same rounding rules as sincos_cw).
+__device__ __forceinline__ void sincos_small(float d, float* sn, float* cs) {
+  const float s = d * d;
+  float ps = fmaf(s, 2.7557318844628753e-06f, -1.9841270113829523e-04f);
+  ps = fmaf(s, ps, 8.333333767950535e-03f);
+  ps = fmaf(s, ps, 4.967053879312289e-09f) + -0.1666666716337204f;
+  *sn = fmaf(d * s, ps, d);
+  float pc = fmaf(s, 2.4801587642286904e-05f, -1.3888889225199819e-03f);
+  pc = fmaf(s, pc, -1.2417634698280722e-09f) + 0.0416666679084301f;
+  *cs = fmaf(s, fmaf(s, pc, -0.5f), 1.0f);
+}
+
 __device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<float>& sm, float s,
                                           bool reim, SwavePart<float>& w, Cplx<float>& A) {
   w.j = segment_of(m.kn, sm.knot, s);
   w.t = __fsub_rn(s, sm.knot[w.j]);  // exact (Sterbenz) on the knot grids used here
-  const float4* c4 = reinterpret_cast<const float4*>(&sm.coef[w.j * 16]);
+  const float* seg = &sm.coef[w.j * kSeg32];
+  const float4* c4 = reinterpret_cast<const float4*>(seg);
   const F2 a = cubic_hl(c4[0], c4[1], w.t);
-  const F2 ph = cubic_hl(c4[2], c4[3], w.t);
   if (reim) {
+    const F2 ph = cubic_hl(c4[2], c4[3], w.t);
     A.re += a.hi + a.lo;
     A.im += ph.hi + ph.lo;
     return;
   }
-  sincos_cw(ph.hi, ph.lo, &w.sn, &w.cs);
+  if (seg[20] != 0.0f) {
+    // e^{i phi} = e^{i phi_ref} e^{i delta}, delta = phi - phi_ref (the phase
+    // cubic without its hi constant term; small over this segment)
+    const float4 h = c4[2], l = c4[3], e = c4[4];  // e: cos phi_ref hi/lo, sin phi_ref hi/lo
+    const float tq = fmaf(fmaf(h.w, w.t, h.z), w.t, h.y) * w.t;
+    const float pl = fmaf(fmaf(fmaf(l.w, w.t, l.z), w.t, l.y), w.t, l.x);
+    float sd, cd;
+    sincos_small(tq + pl, &sd, &cd);
+    w.cs = fmaf(e.x, cd, fmaf(e.y, cd, -fmaf(e.z, sd, e.w * sd)));
+    w.sn = fmaf(e.z, cd, fmaf(e.w, cd, fmaf(e.x, sd, e.y * sd)));
+  } else {
+    const F2 ph = cubic_hl(c4[2], c4[3], w.t);
+    sincos_cw(ph.hi, ph.lo, &w.sn, &w.cs);
+  }
   w.a = a.hi;
   A.re += mul_hl(a.hi, a.lo, w.cs);
   A.im += mul_hl(a.hi, a.lo, w.sn);

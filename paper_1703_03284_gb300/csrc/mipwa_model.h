@@ -99,13 +99,18 @@ struct SplineLU {
 // followed by 2R doubles (Re c_r, Im c_r).
 MIPWA_HD inline int coef_size(int n_knots, int n_res) { return 8 * (n_knots - 1) + 2 * n_res; }
 
-// FP32 form, written by the same kernel as floats: per segment 16 values,
-// magnitude hi[4] lo[4] then phase hi[4] lo[4], each cubic re-expanded about
-// the float-rounded knot float(s_j) so that t = s - float(s_j) is exact;
-// followed by 4 floats per resonance: (Re c'_r hi, lo, Im c'_r hi, lo),
-// c'_r = c_r cscale_r.
+// FP32 form, written by the same kernel as floats: per segment kSeg32 = 24
+// values: magnitude hi[4] lo[4], phase hi[4] lo[4] (each cubic re-expanded
+// about the float-rounded knot float(s_j), so that t = s - float(s_j) is
+// exact), then cos and sin of phi_ref = the phase cubic's hi constant term as
+// pairs (cos hi, cos lo, sin hi, sin lo), then 1 if the phase stays within
+// kSmallPhase of phi_ref over every t the segment's events can have (else 0),
+// and 3 unused; followed by 4 floats per resonance: (Re c'_r hi, lo,
+// Im c'_r hi, lo), c'_r = c_r cscale_r.
+constexpr int kSeg32 = 24;
+constexpr double kSmallPhase = 0.3;
 MIPWA_HD inline int coef32_size(int n_knots, int n_res) {
-  return 16 * (n_knots - 1) + 4 * n_res;
+  return kSeg32 * (n_knots - 1) + 4 * n_res;
 }
 
 // Width of one per-block partial-sum row:

@@ -30,7 +30,7 @@ constexpr int kWidth = 1 + 2 * kMaxRes + 8 * kMaxSeg;  // widest partial row
 constexpr int kLU = 2 * kMaxSeg + 3 * (kMaxKnots - 2);
 constexpr int kParams = 2 * kMaxRes + 2 * kMaxKnots;
 constexpr int kCoef = 8 * kMaxSeg + 2 * kMaxRes;
-constexpr int kCoef32Doubles = (16 * kMaxSeg + 4 * kMaxRes + 1) / 2;
+constexpr int kCoef32Doubles = (kSeg32 * kMaxSeg + 4 * kMaxRes + 1) / 2;
 
 // Offsets (in doubles) of each region of the scratch array.
 constexpr size_t kOffLU = 0;

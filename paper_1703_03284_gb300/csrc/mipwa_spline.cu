@@ -66,11 +66,34 @@ __global__ void prepare_kernel(const Model m, const double* __restrict__ params,
     b[1] = a[1] + d * (2.0 * a[2] + 3.0 * d * a[3]);
     b[2] = a[2] + 3.0 * d * a[3];
     b[3] = a[3];
-    float* f = coef32 + j * 16 + s * 8;
+    float* f = coef32 + j * kSeg32 + s * 8;
     for (int k = 0; k < 4; ++k) {
       const float hi = (float)b[k];
       f[k] = hi;
       f[4 + k] = (float)(b[k] - (double)hi);
+    }
+    if (s == 1) {
+      // e^{i phi} = e^{i phi_ref} e^{i delta}: cos/sin of phi_ref = float(b0)
+      // as pairs, and whether |delta| = |phi - phi_ref| <= kSmallPhase for
+      // every t of the segment's events (inner segments: [0, h_j] about s_j;
+      // the end segments also carry the plot beyond the end knots)
+      const double ref = (double)f[0];
+      double sn, cs;
+      sincos(ref, &sn, &cs);
+      float* e = coef32 + j * kSeg32 + 16;
+      e[0] = (float)cs;
+      e[1] = (float)(cs - (double)e[0]);
+      e[2] = (float)sn;
+      e[3] = (float)(sn - (double)e[2]);
+      const double sj = (double)(float)m.kn.s[j];
+      double tmax = fabs(m.kn.s[j + 1] - sj) + fabs(sj - m.kn.s[j]);
+      const double s_lo = (m.m1 + m.m2) * (m.m1 + m.m2), s_hi = (m.mD - m.m2) * (m.mD - m.m2);
+      if (j == 0) tmax = fmax(tmax, fabs(s_lo - sj));
+      if (j == nseg - 1) tmax = fmax(tmax, fabs(s_hi - sj));
+      const double dmax = fabs(b[0] - ref) + fabs(b[1]) * tmax + fabs(b[2]) * tmax * tmax +
+                          fabs(b[3]) * tmax * tmax * tmax;
+      e[4] = dmax <= kSmallPhase ? 1.0f : 0.0f;
+      e[5] = e[6] = e[7] = 0.0f;
     }
   }
   for (int k = threadIdx.x; k < 2 * n_res; k += blockDim.x) coef[8 * nseg + k] = params[k];
@@ -78,8 +101,8 @@ __global__ void prepare_kernel(const Model m, const double* __restrict__ params,
   for (int k = threadIdx.x; k < 2 * n_res; k += blockDim.x) {
     const double v = params[k] * m.cscale[k >> 1];
     const float hi = (float)v;
-    coef32[16 * nseg + 2 * k] = hi;
-    coef32[16 * nseg + 2 * k + 1] = (float)(v - (double)hi);
+    coef32[kSeg32 * nseg + 2 * k] = hi;
+    coef32[kSeg32 * nseg + 2 * k + 1] = (float)(v - (double)hi);
   }
 }
 

@@ -410,3 +410,22 @@ def test_fp32_nonuniform_knots_three_resonances():
     norm = synth.uniform_in_plot(spec, 300_000, ins, seed=7, dtype=torch.float32).numpy()
     p2 = truth + 0.02 * np.random.default_rng(3).standard_normal(truth.shape)
     _fp32_vs_oracle(spec, o, data.astype(np.float64), norm.astype(np.float64), [truth, p2])
+
+
+def test_fp32_large_phase_steps_take_the_full_sincos():
+    """Knot phases that jump by 2.5 rad between neighbours: on those segments
+    the phase moves too far from its reference for the short series and the
+    kernel takes the full range reduction; a mixed parameter point exercises
+    both paths in one evaluation (and in one warp at segment boundaries)."""
+    name = "pipipi_n40"
+    spec = P.spec_by_name(name)
+    data = P.data_sample(name, 1_000_000, f32=True)
+    norm = P.uniform_sample(name, 1_000_000, f32=True)
+    R, N = spec.n_res, spec.n_knots
+    truth = synth.true_params(spec)
+    zig = truth.copy()
+    zig[2 * R + N:] = 2.5 * (np.arange(N) % 2)
+    mixed = truth.copy()
+    mixed[2 * R + N + N // 2:] = truth[2 * R + N + N // 2:] + 2.5 * (np.arange(N - N // 2) % 2)
+    _fp32_vs_oracle(spec, P.oracle_for(name), data.astype(np.float64), norm.astype(np.float64),
+                    [zig, mixed])
