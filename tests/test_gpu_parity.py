@@ -416,9 +416,13 @@ def test_fp32_large_phase_steps_take_the_full_sincos():
     """Knot phases that jump by 2.5 rad between neighbours: on those segments
     the phase moves too far from its reference for the short series and the
     kernel takes the full range reduction; a mixed parameter point exercises
-    both paths in one evaluation (and in one warp at segment boundaries)."""
+    both paths in one evaluation (and in one warp at segment boundaries).
+    Per-event |A|^2 is held to 1e-5 relative away from zeros of A and the NLL
+    to 1e-2; the gradient to 1e-3 only: these points put many events next to
+    zeros of A, whose 1/|A|^2 weights magnify the FP32 error of A."""
     name = "pipipi_n40"
     spec = P.spec_by_name(name)
+    o = P.oracle_for(name)
     data = P.data_sample(name, 1_000_000, f32=True)
     norm = P.uniform_sample(name, 1_000_000, f32=True)
     R, N = spec.n_res, spec.n_knots
@@ -427,5 +431,13 @@ def test_fp32_large_phase_steps_take_the_full_sincos():
     zig[2 * R + N:] = 2.5 * (np.arange(N) % 2)
     mixed = truth.copy()
     mixed[2 * R + N + N // 2:] = truth[2 * R + N + N // 2:] + 2.5 * (np.arange(N - N // 2) % 2)
-    _fp32_vs_oracle(spec, P.oracle_for(name), data.astype(np.float64), norm.astype(np.float64),
-                    [zig, mixed])
+    lik = Likelihood(0, F32)
+    lik.set_spec(spec)
+    ev = torch.from_numpy(data[:200_000]).to(DEV)
+    for p in (zig, mixed):
+        got = lik.amp2(p, ev).cpu().numpy()
+        want = o.amp2(p, data[:200_000].astype(np.float64))
+        away = want > 1e-3 * want.mean()
+        assert np.abs(got[away] / want[away] - 1).max() < 1e-5
+    _fp32_vs_oracle(spec, o, data.astype(np.float64), norm.astype(np.float64), [zig, mixed],
+                    grad_tol=1e-3)
