@@ -22,6 +22,13 @@ import synth  # noqa: E402
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_values.json")
 
 
+def GOLDEN_SPECS():
+    """The models frozen here: pi pi pi (10, 30 knots), K pi pi (40), K K K (40)
+    and the Re/Im S-wave form of the 10-knot pi pi pi model."""
+    return (synth.pipipi(10), synth.pipipi(30), synth.kpipi(40), synth.kkk(40),
+            synth.as_reim(synth.pipipi(10)))
+
+
 def lattice(spec, n):
     t = spec.s_lo + (spec.s_hi - spec.s_lo) * (np.arange(n) + 0.5) / n
     a, b = np.meshgrid(t, t, indexing="ij")
@@ -30,7 +37,7 @@ def lattice(spec, n):
 
 def main():
     cases = {}
-    for spec in (synth.pipipi(10), synth.pipipi(30), synth.kpipi(40)):
+    for spec in GOLDEN_SPECS():
         o = oracle.Oracle(spec)
         pts = lattice(spec, 9)
         pts = pts[o.inside(pts)]
@@ -39,8 +46,9 @@ def main():
         data = lattice(spec, 13)
         data = data[o.inside(data)]
         entry = {"events": pts.tolist(), "data": data.tolist(), "norm_side": 40}
+        scale = 0.02 if spec.swave_form == "reim" else 0.05
         for label, p in (("true", synth.true_params(spec)),
-                         ("perturbed", synth.perturbed_params(spec, 3))):
+                         ("perturbed", synth.perturbed_params(spec, 3, scale))):
             A = o.amp(p, pts)
             v, g = o.nll_grad(p, data, norm, threads=1)
             entry[label] = {"params": p.tolist(), "amp_re": A.real.tolist(),

@@ -530,7 +530,8 @@ def test_oracle_reproduces_frozen_values():
     path = os.path.join(os.path.dirname(__file__), "golden", "oracle_values.json")
     with open(path) as f:
         cases = json.load(f)
-    specs = {s.name: s for s in (synth.pipipi(10), synth.pipipi(30), synth.kpipi(40))}
+    specs = {s.name: s for s in (synth.pipipi(10), synth.pipipi(30), synth.kpipi(40),
+                                 synth.kkk(40), synth.as_reim(synth.pipipi(10)))}
     for name, entry in cases.items():
         spec = specs[name]
         o = oracle.Oracle(spec)
