@@ -63,7 +63,7 @@ HBM_GBS = _measured_hbm_gbs()
 # from one ncu capture on 2e7 + 2e7 events (profiles/eval_kernel_f32_grad_pipipi_n40.md),
 # scaled to this workload by the events processed (x5); None once the kernel
 # has changed since the capture.
-TRAFFIC_PER_LAUNCH = 1.622e9
+TRAFFIC_PER_LAUNCH = 1.620e9
 
 
 def parse():
