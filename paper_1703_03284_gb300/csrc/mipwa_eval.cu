@@ -561,7 +561,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
             wt = rcp_nr(A2);
           } else {
             sum.add(log(A2));
-            wt = T(1) / A2;
+            wt = A2 >= 2.2250738585072014e-308 ? rcp_d(A2) : T(1) / A2;
           }
         }
       } else {
