@@ -531,8 +531,21 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   int reg_iter = 0;
 #pragma unroll
   for (int k = 0; k < 16; ++k) acc[k] = T(0);
+  // computed basis: the next iteration's event is loaded one iteration ahead
+  // (hides the global-load latency behind this iteration's arithmetic; with
+  // the cached basis the extra registers cost more than they hide)
+  EvT e_next{};
+  if constexpr (!CACHED) {
+    if (first + threadIdx.x < end) e_next = ev[first + threadIdx.x];
+  }
   for (int64_t base = first; base < end; base += stride) {
     const int64_t i = base + threadIdx.x;
+    EvT e = e_next;
+    if constexpr (!CACHED) {
+      if (i + stride < end) e_next = ev[i + stride];
+    } else {
+      if (i < end) e = ev[i];
+    }
     bool ok = false;
     SwaveState<T> sw;
     Cplx<T> A{T(0), T(0)};
@@ -540,7 +553,6 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
     Cplx<double> dBm[BWG ? kMaxRes : 1], dBw[BWG ? kMaxRes : 1];
     T wt = T(1);
     if (i < end) {
-      const EvT e = ev[i];
       const T s12 = (T)e.x, s13 = (T)e.y;
       if constexpr (BWG) {
         bw_basis_deriv(m, (double)s12, (double)s13, B, dBm, dBw);
