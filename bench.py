@@ -34,6 +34,13 @@ WORKLOAD = ("pipipi_n40_1e8_f32: D+->pi-pi+pi+, rho(770) P + f2(1270) D + 40-kno
             "S-wave, 1e8 accept-reject data + 1e8 uniform normalisation events, float32 "
             "(s12,s13)")
 
+
+def workload_name(n):
+    """The workload string for n data + n normalisation events (the default is 1e8)."""
+    if n == 100_000_000:
+        return WORKLOAD
+    return WORKLOAD.replace("1e8", f"{n:.0e}".replace("+0", "").replace("+", ""))
+
 # Algorithmic work per event of one NLL+gradient evaluation of this model
 # (2 resonances, one P- and one D-wave; add/sub/mul = 1, fused multiply-add = 2,
 # each division, square root, sine, cosine and log = 1). Forward: kinematics 24,
@@ -59,11 +66,11 @@ def _measured_hbm_gbs() -> float:
 
 
 HBM_GBS = _measured_hbm_gbs()
-# DRAM bytes (read + write) per launch of the fused FP32 NLL+gradient kernel
-# from one ncu capture on 2e7 + 2e7 events (profiles/eval_kernel_f32_grad_pipipi_n40.md),
-# scaled to this workload by the events processed (x5); None once the kernel
-# has changed since the capture.
-TRAFFIC_PER_LAUNCH = 1.620e9
+# DRAM bytes (read + write) of the fused FP32 NLL+gradient kernel per event
+# processed, from one ncu capture on 2e7 + 2e7 events (324.67 MB per launch,
+# profiles/eval_kernel_f32_grad_pipipi_n40.md); a launch's traffic is this
+# times its events. None once the kernel has changed since the capture.
+TRAFFIC_PER_EVENT = 324.67e6 / 4e7
 
 
 def parse():
@@ -569,7 +576,7 @@ def run(args, world, rank, local, stream):
     achieved = FLOPS_PER_EVENT_GRAD * events / k_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
-                "traffic": TRAFFIC_PER_LAUNCH,
+                "traffic": None if TRAFFIC_PER_EVENT is None else TRAFFIC_PER_EVENT * events,
                 "kernel": "eval_kernel<float,float2,grad>",
                 "kernel_ms": kms / kn,
                 "peak_note": "FP32 from unit counts x 2070 MHz (nominal, not measured)"}
@@ -713,8 +720,9 @@ def run(args, world, rank, local, stream):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_data": n, "n_norm": n,
-                       "l2": "inputs (1.6 GB) larger than L2 (129 MB); no flush needed",
+            "config": {"workload": workload_name(n), "n_data": n, "n_norm": n,
+                       "l2": (f"inputs ({16 * n / 1e9:.2g} GB) larger than L2 (129 MB); no flush needed"
+                              if 16 * n > 129e6 else "inputs fit in L2 (129 MB): not a valid bench size"),
                        "parallelism": f"replicas x{world} (no collective)"},
             "roofline": roofline, "nll_only": nll_only, "fp64_plain": fp64,
             "fp32_cached_basis": cached,
