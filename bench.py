@@ -688,19 +688,42 @@ def run(args, world, rank, local, stream):
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push("e2e")
         g0.record(stream)
+        phases = [0.0, 0.0, 0.0]  # host time in each call (each returns when its work is done)
         for _ in range(args.e2e_steps):
+            t_a = time.perf_counter()
             lik.set_events(data_h)
+            t_b = time.perf_counter()
             lik.set_norm_sample(norm_h)
+            t_c = time.perf_counter()
             lik.nll_grad(params)
+            t_d = time.perf_counter()
+            phases[0] += t_b - t_a
+            phases[1] += t_c - t_b
+            phases[2] += t_d - t_c
         g1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         te = max_over_ranks(g0.elapsed_time(g1), world)
+        # the host link on its own: plain copies of the same pinned buffers
+        scratch = torch.empty_like(data)
+        h2d_gbs = []
+        for buf in (data_h, norm_h):
+            scratch.copy_(buf, non_blocking=True)
+            g0.record(stream)
+            for _ in range(3):
+                scratch.copy_(buf, non_blocking=True)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            h2d_gbs.append(3 * buf.numel() * 4 / (g0.elapsed_time(g1) / 1e3) / 1e9)
+        del scratch
         P = spec.n_params
         e2e = {"value": world * events * args.e2e_steps / (te / 1e3), "unit": "events/s",
                "ms_per_step": te / args.e2e_steps,
                "h2d_bytes_per_step": int(data_h.numel() * 4 + norm_h.numel() * 4 + 8 * P),
-               "d2h_bytes_per_step": int(8 * (1 + P) + 4 + 2 * 8)}
+               "d2h_bytes_per_step": int(8 * (1 + P) + 4 + 2 * 8),
+               "host_link_gbs": {"data": h2d_gbs[0], "norm": h2d_gbs[1]},
+               "host_ms_per_call": {k: 1e3 * v / args.e2e_steps for k, v in
+                                    zip(("set_events", "set_norm_sample", "nll_grad"), phases)}}
 
     toys = None
     if args.toys_steps > 0:

@@ -247,6 +247,22 @@ int mipwa_amp2(mipwa_ctx* ctx, const double* params, const void* d_s12s13, int64
 int mipwa_inside(mipwa_ctx* ctx, const void* d_s12s13, int64_t n, int dtype,
                  uint8_t* d_out);
 
+/* A stored sample (which = MIPWA_SAMPLE_DATA or MIPWA_SAMPLE_NORM) as the
+ * library holds it. Writes its event count to *n and its dtype to *dtype
+ * (either pointer may be NULL) and, if d_out is not NULL, copies its events
+ * in stored order to the DEVICE pointer d_out, which holds n_cap >= *n pairs
+ * of that dtype. With a model set and 2 <= n < 2^31, the stored order groups
+ * the events by spline cell: the stable sort by j12 (N-1) + j13, where j12
+ * and j13 are the S-wave segments (Sec. 2) of s12 and s13, of the order
+ * before (the order given, or, when set_model re-groups a stored sample, its
+ * previous stored order). Otherwise the order is the one given. The likelihood is a sum over events, so the order changes its value
+ * by rounding only. MIPWA_ESTATE if the sample is not set; MIPWA_EINVAL for
+ * a bad `which`, n_cap < *n or a host d_out. Blocks. */
+#define MIPWA_SAMPLE_DATA 0
+#define MIPWA_SAMPLE_NORM 1
+int mipwa_get_sample(mipwa_ctx* ctx, int which, void* d_out, int64_t n_cap, int64_t* n,
+                     int* dtype);
+
 /* Kernel timing (diagnostics, off by default): while on, each evaluation
  * records CUDA events on the context's stream around its fused event kernel;
  * mipwa_kernel_time() returns the summed kernel milliseconds and the number of

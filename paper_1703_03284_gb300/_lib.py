@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libmipwa.so")
 OK, EINVAL, EOUTSIDE, ENONPOS, ECUDA, ETIMEOUT, ESTATE, ENOMEM = 0, -1, -2, -3, -4, -5, -6, -7
 F64, F32 = 0, 1
 SWAVE_MAGPHASE, SWAVE_REIM = 0, 1
+SAMPLE_DATA, SAMPLE_NORM = 0, 1
 MAX_RES = 4
 MAX_KNOTS = 64
 MAX_TOYS = 4096
@@ -55,6 +56,7 @@ SIGNATURES = [
     ("mipwa_set_toys_graph", _i, [_vp, _i]),
     ("mipwa_amp2", _i, [_vp, _pd, _vp, _i64, _i, _vp]),
     ("mipwa_inside", _i, [_vp, _vp, _i64, _i, _vp]),
+    ("mipwa_get_sample", _i, [_vp, _i, _vp, _i64, _pi64, ctypes.POINTER(_i)]),
     ("mipwa_nll_grad_noalloc", _i, [_i, _i, _d, _d, _d, ctypes.POINTER(Resonance), _i, _pd, _i,
                                     _d, _d, _vp, _i64, _vp, _i64, _i, _pd, _vp, _vp]),
     ("mipwa_set_timing", _i, [_vp, _i]),

@@ -269,6 +269,22 @@ class Likelihood:
         del keep
         return out.bool()
 
+    def stored_sample(self, which: str = "data"):
+        """The stored data ("data") or normalisation ("norm") sample as an
+        (n, 2) CUDA tensor in the order the library holds it: grouped by
+        spline cell once a model is set (stable within a cell)."""
+        torch = _torch()
+        code = {"data": _lib.SAMPLE_DATA, "norm": _lib.SAMPLE_NORM}[which]
+        n, dt = ctypes.c_int64(0), ctypes.c_int(0)
+        self._check(self._lib.mipwa_get_sample(self._h, code, None, 0, ctypes.byref(n),
+                                               ctypes.byref(dt)))
+        dtype = torch.float32 if dt.value == _lib.F32 else torch.float64
+        out = torch.empty((n.value, 2), dtype=dtype, device=f"cuda:{self.device}")
+        self._follow_stream()
+        self._check(self._lib.mipwa_get_sample(self._h, code, ctypes.c_void_p(out.data_ptr()),
+                                               n.value, None, None))
+        return out
+
     # ----------------------------------------------------------- diagnostics
     def set_timing(self, on: bool = True):
         self._check(self._lib.mipwa_set_timing(self._h, int(bool(on))))

@@ -1225,6 +1225,25 @@ int mipwa_inside(mipwa_ctx* c, const void* ev, int64_t n, int dtype, uint8_t* ou
   return MIPWA_OK;
 }
 
+int mipwa_get_sample(mipwa_ctx* c, int which, void* out, int64_t n_cap, int64_t* n, int* dtype) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (which != MIPWA_SAMPLE_DATA && which != MIPWA_SAMPLE_NORM)
+    return fail(c, MIPWA_EINVAL, "bad sample %d", which);
+  const mipwa_ctx::Sample& smp = which == MIPWA_SAMPLE_DATA ? c->data : c->norm;
+  if (!smp.set) return fail(c, MIPWA_ESTATE, "the sample is not set");
+  if (n) *n = smp.n;
+  if (dtype) *dtype = smp.dtype;
+  if (!out || smp.n == 0) return MIPWA_OK;
+  if (n_cap < smp.n) return fail(c, MIPWA_EINVAL, "n_cap %lld < %lld events", (long long)n_cap,
+                                 (long long)smp.n);
+  if (!is_device_ptr(out)) return fail(c, MIPWA_EINVAL, "get_sample takes a device pointer");
+  CK(c, cudaMemcpyAsync(out, smp.cur, (size_t)smp.n * ev_bytes(smp.dtype),
+                        cudaMemcpyDeviceToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return MIPWA_OK;
+}
+
 int mipwa_enable_basis_cache(mipwa_ctx* c, int on) {
   int rc = check_ctx(c);
   if (rc) return rc;

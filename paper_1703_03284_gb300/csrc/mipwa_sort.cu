@@ -6,25 +6,22 @@
 // always: the cubic coefficients become shared-memory broadcasts and the spline
 // adjoint can be reduced across the warp before it is binned.
 //
-// Two passes of a stable counting sort (deterministic for a given input): by
-// j12 alone, then by the cell key j12 (N-1) + j13. The result is the single
-// sort by cell key (both passes are stable), but every write goes to a long
-// run: in the first pass a chunk of events spreads over N-1 keys only, and in
-// the second a chunk lies almost entirely in one j12 bucket, so it again
-// meets about N-1 keys (a single pass spreads each chunk over (N-1)^2 keys and
-// writes runs of a few events). Each pass:
-//   1. count:   each warp counts the keys of its contiguous chunk into its
-//               own row of a [chunk][key] table (the first pass of a new
-//               sample also counts the events outside the Dalitz plot);
-//   2. offsets: the table becomes, in place, each (block, key)'s first output
+// A least-significant-digit sort with the segment indices as digits: a stable
+// counting pass by j13, then a stable counting pass by j12, which leaves the
+// events in the order of the cell key j12 (N-1) + j13 with equal keys in the
+// order given (deterministic for a given input). Each pass has N-1 <= 63 keys:
+//   1. count:   a thread block counts the keys of one contiguous chunk into
+//               the chunk's row of a [chunk][key] table (the first pass of a
+//               new sample also counts the events outside the Dalitz plot);
+//   2. offsets: the table becomes, in place, each (chunk, key)'s first output
 //               position: all events of lower keys, plus the events of the
-//               same key in earlier blocks (column sums over groups of
-//               blocks, one scan over keys, then the running sums per group);
-//   3. scatter: each warp walks its chunk in order, 32 events at a time, and
-//               places each event at its key's running offset.
-// kSortWarps chunks share a thread block, each warp with its own
-// shared-memory table (measured on GB300: one warp per block is fastest; eight
-// made the first scatter 15 % slower).
+//               same key in earlier chunks (column sums over groups of
+//               chunks, one scan over keys, then the running sums per group);
+//   3. scatter: a thread block walks its chunk in tiles of consecutive
+//               events, orders each tile by key in shared memory (stably:
+//               warp by warp, row by row, lane by lane) and writes each key's
+//               run of the tile to that key's running output position, so that
+//               neighbouring threads store neighbouring events.
 #include <cuda_runtime.h>
 
 #include "mipwa_amp.cuh"
@@ -32,39 +29,37 @@
 
 namespace mipwa {
 
-constexpr int kSortBlocks = 8192;  // chunks (one warp each); a multiple of kGroup
-constexpr int kSortWarps = 1;      // chunks per thread block (one warp each)
+constexpr int kSortBlocks = 152 * 32;  // chunks; a multiple of kGroup and of 64 pieces
+constexpr int kMaxKeys = 64;           // keys of one pass: N-1 segments
+static_assert(kMaxKnots - 1 <= kMaxKeys, "a pass key must fit the tables");
 
+// events per thread loaded together (64 B of them in flight per thread)
 template <typename EvT>
-__device__ __forceinline__ int cell_key_general(const Knots& kn, const double* knot, const EvT& e) {
-  const int j12 = segment_of(kn, knot, (double)e.x);
-  const int j13 = segment_of(kn, knot, (double)e.y);
-  return j12 * (kn.n - 1) + j13;
+constexpr int kBatch = 64 / (int)sizeof(EvT);
+
+// The S-wave segment of one invariant as the event kernels decide it: FP32
+// arithmetic for float events on evenly spaced knots, FP64 otherwise.
+__device__ __forceinline__ int seg_of(const Knots& kn, float v) {
+  if (kn.uniform) {
+    const float dummy[1] = {0.0f};
+    return segment_of(kn, dummy, v);
+  }
+  return segment_of(kn, kn.s, (double)v);
+}
+
+__device__ __forceinline__ int seg_of(const Knots& kn, double v) {
+  return segment_of(kn, kn.s, v);
 }
 
 template <typename EvT>
 __device__ __forceinline__ int key_of(const Knots& kn, const EvT& e) {
-  if constexpr (std::is_same<EvT, float2>::value) {
-    if (kn.uniform) {  // the FP32 kernels' own segment decision
-      const float dummy[1] = {0.0f};
-      const int j12 = segment_of(kn, dummy, e.x);
-      const int j13 = segment_of(kn, dummy, e.y);
-      return j12 * (kn.n - 1) + j13;
-    }
-  }
-  return cell_key_general(kn, kn.s, e);
+  return seg_of(kn, e.x) * (kn.n - 1) + seg_of(kn, e.y);
 }
 
-// Sort key of a pass: the cell key (FULL) or its j12 part.
-template <typename EvT, bool FULL>
-__device__ __forceinline__ int pass_key(const Knots& kn, const EvT& e) {
-  const int k = key_of(kn, e);
-  return FULL ? k : k / (kn.n - 1);
-}
-
-template <bool FULL>
-__host__ __device__ inline int pass_keys(int n_knots) {
-  return FULL ? (n_knots - 1) * (n_knots - 1) : n_knots - 1;
+// Key of a pass: the segment of s12 (DIGIT 0) or of s13 (DIGIT 1).
+template <typename EvT, int DIGIT>
+__device__ __forceinline__ int digit_of(const Knots& kn, const EvT& e) {
+  return DIGIT == 0 ? seg_of(kn, e.x) : seg_of(kn, e.y);
 }
 
 __host__ __device__ inline int64_t chunk_begin(int64_t n, int b) {
@@ -73,42 +68,56 @@ __host__ __device__ inline int64_t chunk_begin(int64_t n, int b) {
   return v < n ? v : n;
 }
 
-// CHECK: also count the events outside the Dalitz plot into *outside (their
-// keys are clamped segments, so the histogram stays in range).
-template <typename EvT, bool FULL, bool CHECK>
-__global__ void __launch_bounds__(32 * kSortWarps)
-    sort_count_kernel(const Model m, const EvT* ev, int64_t n, int chunk0,
-                      int* counts /* [kSortBlocks][nkeys] */, unsigned long long* outside) {
-  extern __shared__ int hist_all[];
+// One thread block per chunk (kCountThreads threads sharing its histogram):
+// the count is order-free, so a chunk may be counted by many warps, which
+// keeps the SMs full when only a quarter of the chunks (one piece of a sample
+// still arriving) is counted. CHECK: also count the events outside the Dalitz
+// plot into *outside (their keys are clamped segments, so the histogram stays
+// in range).
+constexpr int kCountThreads = 256;
+
+template <typename EvT, int DIGIT, bool CHECK>
+__global__ void __launch_bounds__(kCountThreads)
+    sort_count_kernel(const Model m, const EvT* __restrict__ ev, int64_t n, int chunk0,
+                      int* counts /* [kSortBlocks][N-1] */, unsigned long long* outside) {
+  __shared__ int hist[kMaxKeys];
+  constexpr int B = kBatch<EvT>;
   const Knots& kn = m.kn;
-  const int nkeys = pass_keys<FULL>(kn.n);
-  const int lane = threadIdx.x & 31;
-  const int chunk = chunk0 + blockIdx.x * kSortWarps + (threadIdx.x >> 5);
-  int* hist = hist_all + (threadIdx.x >> 5) * nkeys;
-  for (int k = lane; k < nkeys; k += 32) hist[k] = 0;
-  __syncwarp();
+  const int nkeys = kn.n - 1;
+  const int chunk = chunk0 + blockIdx.x;
+  if (threadIdx.x < kMaxKeys) hist[threadIdx.x] = 0;
+  __syncthreads();
   const int64_t b0 = chunk_begin(n, chunk), b1 = chunk_begin(n, chunk + 1);
   unsigned int out = 0;
-  for (int64_t i = b0 + lane; i < b1; i += 32) {
-    const EvT e = ev[i];
-    atomicAdd(&hist[pass_key<EvT, FULL>(kn, e)], 1);
-    if constexpr (CHECK) {
-      bool in;
-      if constexpr (std::is_same<EvT, float2>::value) in = inside_plot_fast(m, e.x, e.y);
-      else in = inside_plot(m, e.x, e.y);
-      out += in ? 0u : 1u;
+  for (int64_t base = b0 + threadIdx.x; base < b1; base += kCountThreads * B) {
+    EvT e[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (base + kCountThreads * u < b1) e[u] = ev[base + kCountThreads * u];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      if (base + kCountThreads * u < b1) {
+        atomicAdd(&hist[digit_of<EvT, DIGIT>(kn, e[u])], 1);
+        if constexpr (CHECK) {
+          bool in;
+          if constexpr (std::is_same<EvT, float2>::value) in = inside_plot_fast(m, e[u].x, e[u].y);
+          else in = inside_plot(m, e[u].x, e[u].y);
+          out += in ? 0u : 1u;
+        }
+      }
     }
   }
-  __syncwarp();
-  for (int k = lane; k < nkeys; k += 32) counts[(size_t)chunk * nkeys + k] = hist[k];
+  __syncthreads();
+  if (threadIdx.x < nkeys) counts[(size_t)chunk * nkeys + threadIdx.x] = hist[threadIdx.x];
   if constexpr (CHECK) {
     for (int off = 16; off > 0; off >>= 1) out += __shfl_down_sync(0xffffffffu, out, off);
-    if (lane == 0 && out) atomicAdd(outside, (unsigned long long)out);
+    if ((threadIdx.x & 31) == 0 && out) atomicAdd(outside, (unsigned long long)out);
   }
 }
 
 constexpr int kGroup = 64;                        // blocks per column-sum group
-constexpr int kGroups = kSortBlocks / kGroup;     // 128
+constexpr int kGroups = kSortBlocks / kGroup;     // 76
+static_assert(kSortBlocks % kGroup == 0, "kGroup must divide kSortBlocks");
 
 // group_sum[g][k] = sum of counts[b][k] over the blocks b of group g.
 __global__ void __launch_bounds__(256) sort_group_sums(const int* counts, int nkeys, int* group_sum) {
@@ -120,6 +129,10 @@ __global__ void __launch_bounds__(256) sort_group_sums(const int* counts, int nk
   group_sum[(size_t)g * nkeys + k] = t;
 }
 
+// group sums read together before any is overwritten
+constexpr int kScanChunk = 19;
+static_assert(kGroups % kScanChunk == 0, "kScanChunk must divide kGroups");
+
 // One block: per key, the exclusive scan of its group sums (in place) and its
 // total; then the exclusive scan of the totals over keys -> key_start.
 __global__ void __launch_bounds__(1024) sort_key_starts(int* group_sum, int nkeys, int* key_start) {
@@ -127,10 +140,15 @@ __global__ void __launch_bounds__(1024) sort_key_starts(int* group_sum, int nkey
   __shared__ int carry;
   for (int k = threadIdx.x; k < nkeys; k += blockDim.x) {
     int run = 0;
-    for (int g = 0; g < kGroups; ++g) {
-      const int v = group_sum[(size_t)g * nkeys + k];
-      group_sum[(size_t)g * nkeys + k] = run;
-      run += v;
+    for (int g0 = 0; g0 < kGroups; g0 += kScanChunk) {
+      int v[kScanChunk];
+#pragma unroll
+      for (int g = 0; g < kScanChunk; ++g) v[g] = group_sum[(size_t)(g0 + g) * nkeys + k];
+#pragma unroll
+      for (int g = 0; g < kScanChunk; ++g) {
+        group_sum[(size_t)(g0 + g) * nkeys + k] = run;
+        run += v[g];
+      }
     }
     key_start[k] = run;  // total for now
   }
@@ -175,45 +193,125 @@ __global__ void __launch_bounds__(256) sort_offsets(int* counts, int nkeys, cons
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int g = blockIdx.y;
   if (k >= nkeys) return;
+  int v[kGroup];  // read the group's column before overwriting it
+#pragma unroll
+  for (int b = 0; b < kGroup; ++b) v[b] = counts[(size_t)(g * kGroup + b) * nkeys + k];
   int run = key_start[k] + group_sum[(size_t)g * nkeys + k];
-  for (int b = g * kGroup; b < (g + 1) * kGroup; ++b) {
-    const int v = counts[(size_t)b * nkeys + k];
-    counts[(size_t)b * nkeys + k] = run;
-    run += v;
+#pragma unroll
+  for (int b = 0; b < kGroup; ++b) {
+    counts[(size_t)(g * kGroup + b) * nkeys + k] = run;
+    run += v[b];
   }
 }
 
-template <typename EvT, bool FULL>
-__global__ void __launch_bounds__(32 * kSortWarps)
-    sort_scatter_kernel(const Knots kn, const EvT* src, int64_t n, const int* offsets, EvT* dst) {
-  extern __shared__ int cursor_all[];
-  const int nkeys = pass_keys<FULL>(kn.n);
-  const int lane = threadIdx.x & 31, chunk = blockIdx.x * kSortWarps + (threadIdx.x >> 5);
-  int* cursor = cursor_all + (threadIdx.x >> 5) * nkeys;
-  for (int k = lane; k < nkeys; k += 32) cursor[k] = offsets[(size_t)chunk * nkeys + k];
-  __syncwarp();
-  const int64_t b0 = chunk_begin(n, chunk), b1 = chunk_begin(n, chunk + 1);
+// Scatter of one pass: one thread block per chunk, tiles of kTileRows rows of
+// 32 consecutive events per warp (a warp's rows are consecutive, warp w after
+// warp w-1), so the order (warp, row, lane) is the event order.
+constexpr int kScatterThreads = 256;
+constexpr int kScatterWarps = kScatterThreads / 32;
+template <typename EvT>
+constexpr int kTileRows = kBatch<EvT>;
+template <typename EvT>
+constexpr int kTile = kScatterThreads * kTileRows<EvT>;
+
+template <typename EvT, int DIGIT>
+__global__ void __launch_bounds__(kScatterThreads)
+    sort_scatter_kernel(const Knots kn, const EvT* __restrict__ src, int64_t n,
+                        const int* __restrict__ offsets, EvT* __restrict__ dst) {
+  constexpr int R = kTileRows<EvT>, T = kTile<EvT>;
+  __shared__ EvT stage[T];               // the tile in key order
+  __shared__ unsigned char skey[T];      // and the key of each
+  __shared__ int whist[kScatterWarps][kMaxKeys];  // per warp: count, then events before it
+  __shared__ int tile_start[kMaxKeys];   // first tile position of each key
+  __shared__ int tile_count[kMaxKeys];
+  __shared__ int cursor[kMaxKeys];       // next output position of each key
+  const int nkeys = kn.n - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lane_lt = (1u << lane) - 1u;
-  for (int64_t base = b0; base < b1; base += 32) {
-    const int64_t i = base + lane;
-    const bool live = i < b1;
-    const unsigned active = __ballot_sync(0xffffffffu, live);
-    EvT e{};
-    int key = -1 - lane;  // distinct dummy keys for idle lanes
-    if (live) {
-      e = src[i];
-      key = pass_key<EvT, FULL>(kn, e);
+  if (threadIdx.x < nkeys) cursor[threadIdx.x] = offsets[(size_t)blockIdx.x * nkeys + threadIdx.x];
+  const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
+  for (int64_t t0 = b0; t0 < b1; t0 += T) {
+    for (int i = threadIdx.x; i < kScatterWarps * kMaxKeys; i += kScatterThreads)
+      (&whist[0][0])[i] = 0;
+    __syncthreads();
+    // load R rows per warp, then rank each event among the earlier events of
+    // its key in this warp's rows
+    const int64_t wbase = t0 + (int64_t)warp * 32 * R + lane;
+    EvT e[R];
+    int key[R], rank[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+      if (wbase + 32 * u < b1) e[u] = __ldcs(src + wbase + 32 * u);
+#pragma unroll
+    for (int u = 0; u < R; ++u) key[u] = wbase + 32 * u < b1 ? digit_of<EvT, DIGIT>(kn, e[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const bool live = wbase + 32 * u < b1;
+      unsigned peers = __ballot_sync(0xffffffffu, live);  // live lanes with the same key
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        const bool bit = (key[u] >> b) & 1;
+        const unsigned vb = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? vb : ~vb;
+      }
+      const int before = live ? whist[warp][key[u]] : 0;
+      __syncwarp();
+      rank[u] = before + __popc(peers & lane_lt);
+      if (live && lane == 31 - __clz(peers)) whist[warp][key[u]] = before + __popc(peers);
+      __syncwarp();
     }
-    const unsigned same = __match_any_sync(0xffffffffu, key) & active;
-    if (live) {
-      const int rank = __popc(same & lane_lt);
-      const int leader = __ffs(same) - 1;
-      const int base_pos = cursor[key];
-      dst[base_pos + rank] = e;
-      __syncwarp(same);
-      if (lane == leader) cursor[key] = base_pos + __popc(same);
+    __syncthreads();
+    // per key: events of earlier warps (in place), the tile's count, and the
+    // exclusive scan of the counts over keys
+    if (warp == 0) {
+      int c[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        int run = 0;
+        if (k < nkeys) {
+#pragma unroll
+          for (int w = 0; w < kScatterWarps; ++w) {
+            const int v = whist[w][k];
+            whist[w][k] = run;
+            run += v;
+          }
+        }
+        c[h] = run;
+      }
+      int s0 = c[0], s1 = c[1];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y0 = __shfl_up_sync(0xffffffffu, s0, off);
+        const int y1 = __shfl_up_sync(0xffffffffu, s1, off);
+        if (lane >= off) {
+          s0 += y0;
+          s1 += y1;
+        }
+      }
+      s1 += __shfl_sync(0xffffffffu, s0, 31);
+      tile_start[lane] = s0 - c[0];
+      tile_start[lane + 32] = s1 - c[1];
+      tile_count[lane] = c[0];
+      tile_count[lane + 32] = c[1];
     }
-    __syncwarp();
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      if (wbase + 32 * u < b1) {
+        const int p = tile_start[key[u]] + whist[warp][key[u]] + rank[u];
+        stage[p] = e[u];
+        skey[p] = (unsigned char)key[u];
+      }
+    }
+    __syncthreads();
+    const int tn = (int)(b1 - t0 < T ? b1 - t0 : T);
+    for (int j = threadIdx.x; j < tn; j += kScatterThreads) {
+      const int k = skey[j];
+      dst[cursor[k] + (j - tile_start[k])] = stage[j];
+    }
+    __syncthreads();
+    if (threadIdx.x < nkeys) cursor[threadIdx.x] += tile_count[threadIdx.x];
   }
 }
 
@@ -244,53 +342,47 @@ cudaError_t launch_cell_bounds(int ev_f32, const Knots& kn, const void* ev, int6
 }
 
 cudaError_t sort_workspace_ints(int n_knots, size_t* ints) {
-  const int nkeys = (n_knots - 1) * (n_knots - 1);
+  const int nkeys = n_knots - 1;
   // counts [kSortBlocks][nkeys], group sums [kGroups][nkeys], key starts [nkeys]
   *ints = (size_t)nkeys * (kSortBlocks + kGroups + 1);
   return cudaSuccess;
 }
 
-// Count the chunks [c0, c1) (multiples of kSortWarps).
-template <typename EvT, bool FULL, bool CHECK>
+// The first pass sorts by j13, the second by j12.
+constexpr int kFirstDigit = 1, kSecondDigit = 0;
+
+// Count the chunks [c0, c1).
+template <typename EvT, int DIGIT, bool CHECK>
 static cudaError_t count_pass(const Model& m, const EvT* src, int64_t n, int* work,
                               unsigned long long* outside, cudaStream_t st, int c0 = 0,
                               int c1 = kSortBlocks) {
-  const size_t smem = (size_t)kSortWarps * pass_keys<FULL>(m.kn.n) * sizeof(int);
-  auto kern = sort_count_kernel<EvT, FULL, CHECK>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(c1 - c0) / kSortWarps, 32 * kSortWarps, smem, st>>>(m, src, n, c0, work, outside);
+  sort_count_kernel<EvT, DIGIT, CHECK><<<c1 - c0, kCountThreads, 0, st>>>(m, src, n, c0, work,
+                                                                         outside);
   return cudaGetLastError();
 }
 
 // Offsets and scatter of one pass whose counts are in `work`.
-template <typename EvT, bool FULL>
+template <typename EvT, int DIGIT>
 static cudaError_t finish_pass(const Knots& kn, const EvT* src, int64_t n, EvT* dst, int* work,
                                cudaStream_t st) {
-  const int nkeys = pass_keys<FULL>(kn.n);
-  const size_t smem = (size_t)kSortWarps * nkeys * sizeof(int);
+  const int nkeys = kn.n - 1;
   int* group_sum = work + (size_t)nkeys * kSortBlocks;
   int* key_start = group_sum + (size_t)nkeys * kGroups;
   const dim3 cgrid((nkeys + 255) / 256, kGroups);
   sort_group_sums<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum);
   sort_key_starts<<<1, 1024, 0, st>>>(group_sum, nkeys, key_start);
   sort_offsets<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum, key_start);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  auto kern = sort_scatter_kernel<EvT, FULL>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<kSortBlocks / kSortWarps, 32 * kSortWarps, smem, st>>>(kn, src, n, work, dst);
+  sort_scatter_kernel<EvT, DIGIT><<<kSortBlocks, kScatterThreads, 0, st>>>(kn, src, n, work, dst);
   return cudaGetLastError();
 }
 
-// Both passes after the first count: src -> tmp by j12, tmp -> dst by cell.
+// Both passes after the first count: src -> tmp by j13, tmp -> dst by j12.
 template <typename EvT>
 static cudaError_t sort_rest(const Model& m, const EvT* src, int64_t n, EvT* tmp, EvT* dst,
                              int* work, cudaStream_t st) {
-  cudaError_t e = finish_pass<EvT, false>(m.kn, src, n, tmp, work, st);
-  if (e == cudaSuccess) e = count_pass<EvT, true, false>(m, tmp, n, work, nullptr, st);
-  if (e == cudaSuccess) e = finish_pass<EvT, true>(m.kn, tmp, n, dst, work, st);
+  cudaError_t e = finish_pass<EvT, kFirstDigit>(m.kn, src, n, tmp, work, st);
+  if (e == cudaSuccess) e = count_pass<EvT, kSecondDigit, false>(m, tmp, n, work, nullptr, st);
+  if (e == cudaSuccess) e = finish_pass<EvT, kSecondDigit>(m.kn, tmp, n, dst, work, st);
   return e;
 }
 
@@ -299,8 +391,10 @@ cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* sr
                                       int piece, int n_pieces) {
   const int c0 = kSortBlocks / n_pieces * piece, c1 = kSortBlocks / n_pieces * (piece + 1);
   if (ev_f32)
-    return count_pass<float2, false, true>(m, (const float2*)src, n, work, outside, st, c0, c1);
-  return count_pass<double2, false, true>(m, (const double2*)src, n, work, outside, st, c0, c1);
+    return count_pass<float2, kFirstDigit, true>(m, (const float2*)src, n, work, outside, st, c0,
+                                                 c1);
+  return count_pass<double2, kFirstDigit, true>(m, (const double2*)src, n, work, outside, st, c0,
+                                                c1);
 }
 
 int64_t sort_piece_begin(int64_t n, int piece, int n_pieces) {
@@ -317,8 +411,10 @@ cudaError_t launch_sort_rest(int ev_f32, const Model& m, const void* src, int64_
 cudaError_t launch_sort(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
                         void* dst, int* work, cudaStream_t st) {
   cudaError_t e;
-  if (ev_f32) e = count_pass<float2, false, false>(m, (const float2*)src, n, work, nullptr, st);
-  else e = count_pass<double2, false, false>(m, (const double2*)src, n, work, nullptr, st);
+  if (ev_f32)
+    e = count_pass<float2, kFirstDigit, false>(m, (const float2*)src, n, work, nullptr, st);
+  else
+    e = count_pass<double2, kFirstDigit, false>(m, (const double2*)src, n, work, nullptr, st);
   if (e != cudaSuccess) return e;
   return launch_sort_rest(ev_f32, m, src, n, tmp, dst, work, st);
 }
