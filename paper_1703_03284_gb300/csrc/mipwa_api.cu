@@ -59,7 +59,7 @@ struct mipwa_ctx {
   // host-to-device copies of new samples run here, so that one sample's copy
   // overlaps the previous sample's sort on the context stream
   cudaStream_t copy_stream = nullptr;
-  static constexpr int kCopyPieces = 4;  // a sorted sample arrives in pieces, each counted on arrival
+  static constexpr int kCopyPieces = 8;  // a sorted sample arrives in pieces, each counted on arrival
   cudaEvent_t piece_done[kCopyPieces] = {};
   bool basis_on = false;
   // Re/Im form: normalisation from per-cell moments of the normalisation sample
