@@ -77,7 +77,7 @@ __host__ __device__ inline int64_t chunk_begin(int64_t n, int b) {
 constexpr int kCountThreads = 256;
 
 template <typename EvT, int DIGIT, bool CHECK>
-__global__ void __launch_bounds__(kCountThreads)
+__global__ void __launch_bounds__(kCountThreads, 4)
     sort_count_kernel(const Model m, const EvT* __restrict__ ev, int64_t n, int chunk0,
                       int* counts /* [kSortBlocks][N-1] */, unsigned long long* outside) {
   __shared__ int hist[kMaxKeys];
@@ -214,105 +214,126 @@ constexpr int kTileRows = kBatch<EvT>;
 template <typename EvT>
 constexpr int kTile = kScatterThreads * kTileRows<EvT>;
 
-template <typename EvT, int DIGIT>
-__global__ void __launch_bounds__(kScatterThreads)
-    sort_scatter_kernel(const Knots kn, const EvT* __restrict__ src, int64_t n,
-                        const int* __restrict__ offsets, EvT* __restrict__ dst) {
-  constexpr int R = kTileRows<EvT>, T = kTile<EvT>;
-  __shared__ EvT stage[T];               // the tile in key order
-  __shared__ unsigned char skey[T];      // and the key of each
-  __shared__ int whist[kScatterWarps][kMaxKeys];  // per warp: count, then events before it
-  __shared__ int tile_start[kMaxKeys];   // first tile position of each key
-  __shared__ int tile_count[kMaxKeys];
-  __shared__ int cursor[kMaxKeys];       // next output position of each key
-  const int nkeys = kn.n - 1;
+template <typename EvT>
+struct ScatterSmem {
+  EvT stage[kTile<EvT>];                // the tile in key order
+  unsigned char skey[kTile<EvT>];       // and the key of each
+  int whist[kScatterWarps][kMaxKeys];   // per warp: count, then its first tile position
+  int delta[kMaxKeys];                  // output position - tile position, per key
+  int cursor[kMaxKeys];                 // next output position of each key
+};
+
+// One tile of tn events starting at src (FULL: tn = kTile, no bounds checks).
+template <typename EvT, int DIGIT, bool FULL>
+__device__ __forceinline__ void scatter_tile(ScatterSmem<EvT>& sm, const Knots& kn, int nkeys,
+                                             const EvT* __restrict__ src, int tn,
+                                             EvT* __restrict__ dst) {
+  constexpr int R = kTileRows<EvT>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lane_lt = (1u << lane) - 1u;
-  if (threadIdx.x < nkeys) cursor[threadIdx.x] = offsets[(size_t)blockIdx.x * nkeys + threadIdx.x];
-  const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
-  for (int64_t t0 = b0; t0 < b1; t0 += T) {
-    for (int i = threadIdx.x; i < kScatterWarps * kMaxKeys; i += kScatterThreads)
-      (&whist[0][0])[i] = 0;
-    __syncthreads();
-    // load R rows per warp, then rank each event among the earlier events of
-    // its key in this warp's rows
-    const int64_t wbase = t0 + (int64_t)warp * 32 * R + lane;
-    EvT e[R];
-    int key[R], rank[R];
+  // the previous tile's last reads of this warp's row are done (barrier 3)
+  sm.whist[warp][lane] = 0;
+  sm.whist[warp][lane + 32] = 0;
+  __syncwarp();
+  const int wbase = warp * 32 * R + lane;
+  EvT e[R];
+  int kr[R];  // the key (bits 0-7), then also the rank (bits 8 and up)
 #pragma unroll
-    for (int u = 0; u < R; ++u)
-      if (wbase + 32 * u < b1) e[u] = __ldcs(src + wbase + 32 * u);
+  for (int u = 0; u < R; ++u)
+    if (FULL || wbase + 32 * u < tn) e[u] = __ldcs(src + wbase + 32 * u);
 #pragma unroll
-    for (int u = 0; u < R; ++u) key[u] = wbase + 32 * u < b1 ? digit_of<EvT, DIGIT>(kn, e[u]) : 0;
+  for (int u = 0; u < R; ++u)
+    kr[u] = (FULL || wbase + 32 * u < tn) ? digit_of<EvT, DIGIT>(kn, e[u]) : 0;
+  // rank of each event among the earlier events of its key in this warp's
+  // rows: the live lanes of a row with the same key, from six ballots
 #pragma unroll
-    for (int u = 0; u < R; ++u) {
-      const bool live = wbase + 32 * u < b1;
-      unsigned peers = __ballot_sync(0xffffffffu, live);  // live lanes with the same key
+  for (int u = 0; u < R; ++u) {
+    const bool live = FULL || wbase + 32 * u < tn;
+    const int key = kr[u];
+    unsigned peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, live);
 #pragma unroll
-      for (int b = 0; b < 6; ++b) {
-        const bool bit = (key[u] >> b) & 1;
-        const unsigned vb = __ballot_sync(0xffffffffu, bit);
-        peers &= bit ? vb : ~vb;
-      }
-      const int before = live ? whist[warp][key[u]] : 0;
-      __syncwarp();
-      rank[u] = before + __popc(peers & lane_lt);
-      if (live && lane == 31 - __clz(peers)) whist[warp][key[u]] = before + __popc(peers);
-      __syncwarp();
+    for (int b = 0; b < 6; ++b) {
+      const bool bit = (key >> b) & 1;
+      const unsigned vb = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? vb : ~vb;
     }
-    __syncthreads();
-    // per key: events of earlier warps (in place), the tile's count, and the
-    // exclusive scan of the counts over keys
-    if (warp == 0) {
-      int c[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int k = lane + 32 * h;
-        int run = 0;
-        if (k < nkeys) {
-#pragma unroll
-          for (int w = 0; w < kScatterWarps; ++w) {
-            const int v = whist[w][k];
-            whist[w][k] = run;
-            run += v;
-          }
-        }
-        c[h] = run;
-      }
-      int s0 = c[0], s1 = c[1];
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int y0 = __shfl_up_sync(0xffffffffu, s0, off);
-        const int y1 = __shfl_up_sync(0xffffffffu, s1, off);
-        if (lane >= off) {
-          s0 += y0;
-          s1 += y1;
-        }
-      }
-      s1 += __shfl_sync(0xffffffffu, s0, 31);
-      tile_start[lane] = s0 - c[0];
-      tile_start[lane + 32] = s1 - c[1];
-      tile_count[lane] = c[0];
-      tile_count[lane + 32] = c[1];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-      if (wbase + 32 * u < b1) {
-        const int p = tile_start[key[u]] + whist[warp][key[u]] + rank[u];
-        stage[p] = e[u];
-        skey[p] = (unsigned char)key[u];
-      }
-    }
-    __syncthreads();
-    const int tn = (int)(b1 - t0 < T ? b1 - t0 : T);
-    for (int j = threadIdx.x; j < tn; j += kScatterThreads) {
-      const int k = skey[j];
-      dst[cursor[k] + (j - tile_start[k])] = stage[j];
-    }
-    __syncthreads();
-    if (threadIdx.x < nkeys) cursor[threadIdx.x] += tile_count[threadIdx.x];
+    const int before = sm.whist[warp][key];
+    __syncwarp();
+    kr[u] = key | ((before + __popc(peers & lane_lt)) << 8);
+    if (live && lane == 31 - __clz(peers)) sm.whist[warp][key] = before + __popc(peers);
+    __syncwarp();
   }
+  __syncthreads();  // barrier 1: every warp's counts are in
+  // warp 0, two keys per lane: each warp's first tile position per key (the
+  // tile's exclusive scan over keys plus the events of earlier warps), the
+  // offset from tile to output position, and the cursor moved past the tile
+  if (warp == 0) {
+    int c[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int run = 0;
+#pragma unroll
+      for (int w = 0; w < kScatterWarps; ++w) run += sm.whist[w][lane + 32 * h];
+      c[h] = run;
+    }
+    int s0 = c[0], s1 = c[1];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y0 = __shfl_up_sync(0xffffffffu, s0, off);
+      const int y1 = __shfl_up_sync(0xffffffffu, s1, off);
+      if (lane >= off) {
+        s0 += y0;
+        s1 += y1;
+      }
+    }
+    s1 += __shfl_sync(0xffffffffu, s0, 31);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      int run = h == 0 ? s0 - c[0] : s1 - c[1];  // the tile's first position of key k
+      if (k < nkeys) {
+        sm.delta[k] = sm.cursor[k] - run;
+        sm.cursor[k] += c[h];
+      }
+#pragma unroll
+      for (int w = 0; w < kScatterWarps; ++w) {
+        const int v = sm.whist[w][k];
+        sm.whist[w][k] = run;
+        run += v;
+      }
+    }
+  }
+  __syncthreads();  // barrier 2: positions known
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    if (FULL || wbase + 32 * u < tn) {
+      const int key = kr[u] & 0xff;
+      const int p = sm.whist[warp][key] + (kr[u] >> 8);
+      sm.stage[p] = e[u];
+      sm.skey[p] = (unsigned char)key;
+    }
+  }
+  __syncthreads();  // barrier 3: the tile is in key order
+  for (int j = threadIdx.x; j < (FULL ? kTile<EvT> : tn); j += kScatterThreads)
+    dst[sm.delta[sm.skey[j]] + j] = sm.stage[j];
+}
+
+template <typename EvT, int DIGIT>
+__global__ void __launch_bounds__(kScatterThreads, 3)
+    sort_scatter_kernel(const Knots kn, const EvT* __restrict__ src, int64_t n,
+                        const int* __restrict__ offsets, EvT* __restrict__ dst) {
+  constexpr int T = kTile<EvT>;
+  __shared__ ScatterSmem<EvT> sm;
+  const int nkeys = kn.n - 1;
+  if (threadIdx.x < nkeys)
+    sm.cursor[threadIdx.x] = offsets[(size_t)blockIdx.x * nkeys + threadIdx.x];
+  __syncthreads();
+  const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
+  const int len = (int)(b1 - b0);
+  src += b0;
+  int t0 = 0;
+  for (; t0 + T <= len; t0 += T) scatter_tile<EvT, DIGIT, true>(sm, kn, nkeys, src + t0, T, dst);
+  if (t0 < len) scatter_tile<EvT, DIGIT, false>(sm, kn, nkeys, src + t0, len - t0, dst);
 }
 
 // first[k], last[k] = the index range of key k in a sample grouped by key
