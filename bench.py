@@ -83,7 +83,7 @@ def parse():
                     help="data events (= normalisation events)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--nll-steps", type=int, default=50, help="NLL-only (no gradient) steps")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cached-steps", type=int, default=10)
     ap.add_argument("--toys-steps", type=int, default=3)
     ap.add_argument("--reim-steps", type=int, default=10)
@@ -690,6 +690,7 @@ def run(args, world, rank, local, stream):
         torch.cuda.nvtx.range_push("e2e")
         g0.record(stream)
         phases = [0.0, 0.0, 0.0]  # host time in each call (each returns when its work is done)
+        step_ms = []
         for _ in range(args.e2e_steps):
             t_a = time.perf_counter()
             lik.set_events(data_h)
@@ -701,6 +702,7 @@ def run(args, world, rank, local, stream):
             phases[0] += t_b - t_a
             phases[1] += t_c - t_b
             phases[2] += t_d - t_c
+            step_ms.append(1e3 * (t_d - t_a))
         g1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -724,7 +726,11 @@ def run(args, world, rank, local, stream):
                "d2h_bytes_per_step": int(8 * (1 + P) + 4 + 2 * 8),
                "host_link_gbs": {"data": h2d_gbs[0], "norm": h2d_gbs[1]},
                "host_ms_per_call": {k: 1e3 * v / args.e2e_steps for k, v in
-                                    zip(("set_events", "set_norm_sample", "nll_grad"), phases)}}
+                                    zip(("set_events", "set_norm_sample", "nll_grad"), phases)},
+               # now and then a single step takes 2-5x longer (its host-to-device
+               # copies stall); the mean above includes such steps
+               "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
+                           "max": max(step_ms)}}
 
     toys = None
     if args.toys_steps > 0:
