@@ -90,9 +90,10 @@ def _load():
             lib.oracle_basis.argtypes = [pm, i64, pd, pd]
             lib.oracle_density.argtypes = [pm, pd, i64, pd, pd, i32]
             lib.oracle_nll_grad.argtypes = [pm, pd, i64, pd, i64, pd, pd, pd, i32]
+            lib.oracle_nll_grad_w.argtypes = [pm, pd, i64, pd, i64, pd, pd, pd, pd, i32]
             lib.oracle_nll.argtypes = [pm, pd, i64, pd, i64, pd, pd, i32]
             for f in ("oracle_inside", "oracle_amp", "oracle_basis", "oracle_density",
-                      "oracle_nll_grad", "oracle_nll"):
+                      "oracle_nll_grad", "oracle_nll_grad_w", "oracle_nll"):
                 getattr(lib, f).restype = i32
             _lib = lib
     return _lib
@@ -219,23 +220,30 @@ class Oracle:
     def amp2(self, params, events) -> np.ndarray:
         return np.abs(self.amp(params, events)) ** 2
 
-    def nll(self, params, data, norm, threads: int | None = None) -> float:
-        v, _ = self._nll_grad(params, data, norm, False, threads)
+    def nll(self, params, data, norm, threads: int | None = None, norm_weights=None) -> float:
+        v, _ = self._nll_grad(params, data, norm, False, threads, norm_weights)
         return v
 
-    def nll_grad(self, params, data, norm, threads: int | None = None):
-        return self._nll_grad(params, data, norm, True, threads)
+    def nll_grad(self, params, data, norm, threads: int | None = None, norm_weights=None):
+        """-2 ln L and its gradient; norm_weights (one per normalisation point,
+        None: all 1) make the normalisation integral a weighted mean."""
+        return self._nll_grad(params, data, norm, True, threads, norm_weights)
 
-    def _nll_grad(self, params, data, norm, want_grad, threads):
+    def _nll_grad(self, params, data, norm, want_grad, threads, norm_weights=None):
         p = self._params(params)
         d = _events(data) if len(data) else np.zeros((0, 2))
         n = _events(norm)
+        w = None
+        if norm_weights is not None:
+            w = np.ascontiguousarray(norm_weights, dtype=np.float64)
+            if w.shape != (len(n),):
+                raise ValueError("one weight per normalisation point")
         out = ctypes.c_double()
         g = np.empty(self.n_params) if want_grad else None
-        rc = self.lib.oracle_nll_grad(ctypes.byref(self.m), _pd(p), len(d), _pd(d), len(n),
-                                      _pd(n), ctypes.byref(out),
-                                      _pd(g) if want_grad else None,
-                                      threads or default_threads())
+        rc = self.lib.oracle_nll_grad_w(ctypes.byref(self.m), _pd(p), len(d), _pd(d), len(n),
+                                        _pd(n), _pd(w) if w is not None else None,
+                                        ctypes.byref(out), _pd(g) if want_grad else None,
+                                        threads or default_threads())
         if rc != OK:
             raise ArithmeticError(f"oracle_nll_grad failed ({rc})")
         return out.value, g

@@ -397,10 +397,13 @@ int oracle_density(const oracle_model* md, const double* params, int64_t n,
 }
 
 // -2 ln L = -2 sum_i ln|A(x_i)|^2 + 2 N_data ln I,  I = (1/N_norm) sum_j |A(y_j)|^2.
-// When grad != NULL it also receives d(-2 ln L)/d(params), the analytic adjoint.
-int oracle_nll_grad(const oracle_model* md, const double* params, int64_t n_data,
-                    const double* data, int64_t n_norm, const double* norm, double* nll,
-                    double* grad, int nthreads) {
+// With weights w_j for the normalisation points (norm_w != NULL) the integral is
+// their weighted mean, I = sum_j w_j |A(y_j)|^2 / sum_j w_j (w_j = 1: the plain
+// mean above). When grad != NULL it also receives d(-2 ln L)/d(params), the
+// analytic adjoint.
+int oracle_nll_grad_w(const oracle_model* md, const double* params, int64_t n_data,
+                      const double* data, int64_t n_norm, const double* norm,
+                      const double* norm_w, double* nll, double* grad, int nthreads) {
   if (!valid_model(md) || n_norm <= 0 || n_data < 0) return ORACLE_EINVAL;
   const bool want_grad = grad != nullptr;
   Evaluator ev(md, params, want_grad);
@@ -409,8 +412,8 @@ int oracle_nll_grad(const oracle_model* md, const double* params, int64_t n_data
 
   // Each chunk of kChunk events is summed on its own, then the chunk sums are
   // combined in chunk order: the result is independent of the thread count.
-  auto run = [&](int64_t n, const double* ev_xy, bool is_data, CSum* total, CSum* gtot,
-                 int* bad) {
+  auto run = [&](int64_t n, const double* ev_xy, const double* wts, bool is_data, CSum* total,
+                 CSum* gtot, int* bad) {
     const int64_t nchunk = (n + kChunk - 1) / kChunk;
     std::vector<double> csum(nchunk);
     std::vector<double> cgrad(want_grad ? nchunk * P : 0);
@@ -426,6 +429,7 @@ int oracle_nll_grad(const oracle_model* md, const double* params, int64_t n_data
         const double s12 = ev_xy[2 * i], s13 = ev_xy[2 * i + 1];
         const cplx A = ev.amp(s12, s13);
         const double A2 = std::norm(A);
+        const double wj = wts ? wts[i] : 1.0;  // weight of a normalisation point
         if (is_data) {
           if (!(A2 > 0.0) || !std::isfinite(A2)) {
             cbad[ch] = 1;
@@ -437,11 +441,11 @@ int oracle_nll_grad(const oracle_model* md, const double* params, int64_t n_data
             cbad[ch] = 1;
             continue;
           }
-          s.add(A2);
+          s.add(wj * A2);
         }
         if (want_grad) {
           ev.amp2_grad(s12, s13, A, g.data());
-          const double w = is_data ? 1.0 / A2 : 1.0;
+          const double w = is_data ? 1.0 / A2 : wj;
           for (int k = 0; k < P; ++k) gs[k].add(w * g[k]);
         }
       }
@@ -460,16 +464,25 @@ int oracle_nll_grad(const oracle_model* md, const double* params, int64_t n_data
   CSum sum_log, sum_norm;
   std::vector<CSum> g_data(P), g_norm(P);
   int bad = 0;
-  run(n_data, data, true, &sum_log, g_data.data(), &bad);
-  run(n_norm, norm, false, &sum_norm, g_norm.data(), &bad);
+  run(n_data, data, nullptr, true, &sum_log, g_data.data(), &bad);
+  run(n_norm, norm, norm_w, false, &sum_norm, g_norm.data(), &bad);
   const double S = sum_norm.value();
   if (bad || !(S > 0.0)) return ORACLE_ENONPOS;
-  const double I = S / (double)n_norm;
+  CSum wsum;  // sum of the weights, in event order
+  for (int64_t j = 0; j < n_norm; ++j) wsum.add(norm_w ? norm_w[j] : 1.0);
+  if (!(wsum.value() > 0.0)) return ORACLE_EINVAL;
+  const double I = S / wsum.value();
   *nll = -2.0 * sum_log.value() + 2.0 * (double)n_data * std::log(I);
   if (want_grad)
     for (int k = 0; k < P; ++k)
       grad[k] = -2.0 * g_data[k].value() + 2.0 * (double)n_data * g_norm[k].value() / S;
   return ORACLE_OK;
+}
+
+int oracle_nll_grad(const oracle_model* md, const double* params, int64_t n_data,
+                    const double* data, int64_t n_norm, const double* norm, double* nll,
+                    double* grad, int nthreads) {
+  return oracle_nll_grad_w(md, params, n_data, data, n_norm, norm, nullptr, nll, grad, nthreads);
 }
 
 int oracle_nll(const oracle_model* md, const double* params, int64_t n_data,

@@ -413,6 +413,57 @@ def test_nll_matches_direct_sum():
     assert o.nll(p, data, norm, threads=1) == o.nll(p, data, norm, threads=4)
 
 
+# ------------------------------------------------- weighted normalisation
+# A weight per normalisation point makes the integral a weighted mean,
+# I = sum w_j |A(y_j)|^2 / sum w_j. Integer weights are multiplicities, so they
+# must give exactly the likelihood of the sample with each point repeated.
+@pytest.mark.parametrize("spec", [synth.pipipi(10), synth.as_reim(synth.kpipi(12))],
+                         ids=lambda s: s.name + "_" + s.swave_form)
+def test_integer_weights_equal_repeated_points(spec):
+    o, data, norm = _small_problem(spec)
+    rng = np.random.default_rng(5)
+    k = rng.integers(0, 4, len(norm))
+    k[0] = max(k[0], 1)
+    p = synth.perturbed_params(spec, 19)
+    v, g = o.nll_grad(p, data, norm, norm_weights=k.astype(np.float64))
+    vr, gr = o.nll_grad(p, data, np.repeat(norm, k, axis=0))
+    assert v == pytest.approx(vr, rel=1e-13)
+    np.testing.assert_allclose(g, gr, rtol=1e-11, atol=1e-11 * np.abs(gr).max())
+
+
+def test_constant_weights_equal_unweighted_and_weighted_mean():
+    spec = synth.pipipi(10)
+    o, data, norm = _small_problem(spec, n_data=2000)
+    p = synth.perturbed_params(spec, 23)
+    v0, g0 = o.nll_grad(p, data, norm)
+    v1, g1 = o.nll_grad(p, data, norm, norm_weights=np.full(len(norm), 0.37))
+    assert v1 == pytest.approx(v0, rel=1e-14)
+    np.testing.assert_allclose(g1, g0, rtol=1e-12, atol=1e-12 * np.abs(g0).max())
+    # random weights: the direct numpy statement of the weighted mean
+    w = np.random.default_rng(8).uniform(0.2, 3.0, len(norm))
+    a2 = o.amp2(p, norm)
+    want = -2 * np.sum(np.log(o.amp2(p, data))) + 2 * len(data) * np.log(np.sum(w * a2) / np.sum(w))
+    assert o.nll(p, data, norm, norm_weights=w) == pytest.approx(want, rel=1e-12)
+    with pytest.raises(ArithmeticError):  # no positive total weight
+        o.nll(p, data, norm, norm_weights=np.zeros(len(norm)))
+
+
+def test_weighted_gradient_central_differences():
+    spec = synth.kpipi(12)
+    o, data, norm = _small_problem(spec)
+    w = np.random.default_rng(9).uniform(0.0, 2.0, len(norm))
+    p = synth.perturbed_params(spec, 29)
+    _, g = o.nll_grad(p, data, norm, norm_weights=w)
+    h = 1e-6
+    fd = np.empty_like(p)
+    for k in range(len(p)):
+        e = np.zeros_like(p)
+        e[k] = h
+        fd[k] = (o.nll(p + e, data, norm, norm_weights=w)
+                 - o.nll(p - e, data, norm, norm_weights=w)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-5 * np.abs(g).max())
+
+
 def test_nll_rejects_nonpositive_amplitude():
     knots = synth.uniform_knots(0.078, 2.987, 6)
     spec = synth.ModelSpec(name="zero", mD=synth.M_D, m1=synth.M_PI, m2=synth.M_PI,
