@@ -153,6 +153,20 @@ int mipwa_set_events(mipwa_ctx* ctx, const void* s12s13, int64_t n, int dtype,
 int mipwa_set_norm_sample(mipwa_ctx* ctx, const void* s12s13, int64_t n, int dtype,
                           int on_device, int64_t* n_outside);
 
+/* Normalisation sample with a weight per point: as mipwa_set_norm_sample, plus
+ * `weights`, n values of the events' dtype (float for MIPWA_F32, double for
+ * MIPWA_F64) at a device pointer when on_device != 0, else in host memory;
+ * NULL means every weight is 1. The normalisation integral of Sec. 4 becomes
+ * the weighted mean I = sum_j w_j |A(y_j)|^2 / sum_j w_j (an efficiency-
+ * weighted phase-space sample, say); w_j = 1 is the paper's plain mean. The
+ * weights follow their points into the stored order. Every weight must be
+ * finite and their sum positive; otherwise the call stores nothing and
+ * returns MIPWA_EINVAL (events outside the plot: MIPWA_EOUTSIDE, as for
+ * mipwa_set_norm_sample). A weighted sample is evaluated by the general event
+ * kernels (not the ones specialised for a P- plus D-wave model). */
+int mipwa_set_norm_sample_weighted(mipwa_ctx* ctx, const void* s12s13, const void* weights,
+                                   int64_t n, int dtype, int on_device, int64_t* n_outside);
+
 /* S-wave knot parametrisation (Sec. 2: the S-wave is a cubic spline "in the
  * complex plane" through complex values at the N boundary points).
  *   MIPWA_SWAVE_MAGPHASE (default): knot block [a_k..., phi_k...],

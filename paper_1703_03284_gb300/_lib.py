@@ -57,6 +57,7 @@ SIGNATURES = [
     ("mipwa_amp2", _i, [_vp, _pd, _vp, _i64, _i, _vp]),
     ("mipwa_inside", _i, [_vp, _vp, _i64, _i, _vp]),
     ("mipwa_get_sample", _i, [_vp, _i, _vp, _i64, _pi64, ctypes.POINTER(_i)]),
+    ("mipwa_set_norm_sample_weighted", _i, [_vp, _vp, _vp, _i64, _i, _i, _pi64]),
     ("mipwa_nll_grad_noalloc", _i, [_i, _i, _d, _d, _d, ctypes.POINTER(Resonance), _i, _pd, _i,
                                     _d, _d, _vp, _i64, _vp, _i64, _i, _pd, _vp, _vp]),
     ("mipwa_set_timing", _i, [_vp, _i]),

@@ -156,8 +156,31 @@ class Likelihood:
     def set_events(self, x):
         self._set(self._lib.mipwa_set_events, x)
 
-    def set_norm_sample(self, x):
-        self._set(self._lib.mipwa_set_norm_sample, x)
+    def set_norm_sample(self, x, weights=None):
+        """Normalisation points (n, 2); optional weights (n,), one per point,
+        make the normalisation integral their weighted mean. The weights are
+        converted to the points' dtype and must live where the points do."""
+        if weights is None:
+            self._set(self._lib.mipwa_set_norm_sample, x)
+            return
+        self._follow_stream()
+        ptr, n, code, on_dev, keep = _event_buffer(x)
+        torch = _torch()
+        if on_dev:
+            w = torch.as_tensor(weights, device=keep.device)
+            w = w.to(keep.dtype).contiguous()
+            wptr = w.data_ptr()
+        else:
+            w = np.ascontiguousarray(weights, dtype=np.float32 if code == F32 else np.float64)
+            wptr = w.ctypes.data
+        if w.shape != (n,):
+            raise ValueError("one weight per normalisation point")
+        n_out = ctypes.c_int64(0)
+        rc = self._lib.mipwa_set_norm_sample_weighted(self._h, ctypes.c_void_p(ptr),
+                                                      ctypes.c_void_p(wptr), n, code, on_dev,
+                                                      ctypes.byref(n_out))
+        del keep, w
+        self._check(rc, n_out.value)
 
     def enable_basis_cache(self, on: bool = True):
         self._check(self._lib.mipwa_enable_basis_cache(self._h, int(bool(on))))

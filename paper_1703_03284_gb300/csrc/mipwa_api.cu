@@ -35,6 +35,7 @@ struct mipwa_ctx {
   int* d_flags = nullptr;
   unsigned int* d_counter = nullptr;
   unsigned long long* d_count = nullptr;
+  double* d_wsum = nullptr;  // sum of a new sample's weights (kWeightSumDoubles)
   double* d_partials = nullptr;
   size_t partials_cap = 0;  // doubles
   int* d_sortwork = nullptr;
@@ -55,6 +56,14 @@ struct mipwa_ctx {
     bool basis_valid = false;
     bool no_sort = false;   // keep the caller's order (toy ranges)
     cudaEvent_t spare_free = nullptr;  // recorded after the last kernel that touches `spare`
+    // normalisation sample: a weight per event (the events' scalar type), in
+    // the stored order, double-buffered like the events; wsum = their sum
+    void* w_cur = nullptr;
+    size_t w_cur_cap = 0;
+    void* w_spare = nullptr;
+    size_t w_spare_cap = 0;
+    bool weighted = false;
+    double wsum = 0.0;
   } data, norm, toys;
   // host-to-device copies of new samples run here, so that one sample's copy
   // overlaps the previous sample's sort on the context stream
@@ -323,8 +332,9 @@ int build_gram(mipwa_ctx* c) {
   const int ev32 = smp.dtype == MIPWA_F32;
   CK(c, launch_cell_bounds(ev32, c->model.kn, smp.cur, smp.n, c->d_cells, c->d_cells + nkeys,
                            grid_for(c, smp.n), c->stream));
-  CK(c, launch_gram_build(ev32, c->mode == MIPWA_F32, c->model, smp.cur, c->d_cells,
-                          c->d_cells + nkeys, c->d_gram, c->stream));
+  CK(c, launch_gram_build(ev32, c->mode == MIPWA_F32, c->model, smp.cur,
+                          smp.weighted ? smp.w_cur : nullptr, c->d_cells, c->d_cells + nkeys,
+                          c->d_gram, c->stream));
   c->launches += 2;
   CK(c, cudaStreamSynchronize(c->stream));
   c->gram_valid = true;
@@ -355,7 +365,8 @@ int build_basis(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
 }
 
 int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n, int dtype,
-               int on_device, int64_t* n_outside, bool allow_empty) {
+               int on_device, int64_t* n_outside, bool allow_empty,
+               const void* wptr = nullptr) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (n_outside) *n_outside = 0;
@@ -366,8 +377,17 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
   const size_t bytes = (size_t)n * ev_bytes(dtype);
   rc = ensure(c, &smp.spare, &smp.spare_cap, bytes);
   if (rc) return rc;
+  const bool weighted = wptr != nullptr && n > 0;
+  const size_t wbytes = (size_t)n * (dtype == MIPWA_F32 ? sizeof(float) : sizeof(double));
+  if (weighted) {
+    if (on_device && !is_device_ptr(wptr))
+      return fail(c, MIPWA_EINVAL, "on_device set but the weights are not device memory");
+    rc = ensure(c, &smp.w_spare, &smp.w_spare_cap, wbytes);
+    if (rc) return rc;
+  }
   const bool will_sort = c->have_model && sortable(n) && !smp.no_sort;
-  unsigned long long outside = 0;
+  unsigned long long outside = 0, wbad = 0;
+  double wsum = 0.0;
   if (n > 0) {
     if (on_device) {
       if (!is_device_ptr(ptr))
@@ -412,6 +432,18 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
                           grid_for(c, n), c->stream));
       c->launches++;
     }
+    if (weighted) {
+      // the weights: copied, then summed in FP64 (fixed order) and checked
+      CK(c, cudaMemcpyAsync(smp.w_spare, wptr, wbytes,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            c->stream));
+      CK(c, launch_weight_sum(dtype == MIPWA_F32, smp.w_spare, n, c->d_wsum, c->stream));
+      c->launches += 2;
+      CK(c, cudaMemcpyAsync(&wsum, c->d_wsum + 256, sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+      CK(c, cudaMemcpyAsync(&wbad, c->d_wsum + 257, sizeof(wbad), cudaMemcpyDeviceToHost,
+                            c->stream));
+    }
     CK(c, cudaMemcpyAsync(&outside, c->d_count, sizeof(outside), cudaMemcpyDeviceToHost,
                           c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -421,14 +453,20 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
     return fail(c, MIPWA_EOUTSIDE, "%llu of %lld events lie outside the Dalitz plot", outside,
                 (long long)n);
   }
+  if (weighted && wbad > 0)
+    return fail(c, MIPWA_EINVAL, "%llu of %lld weights are not finite", wbad, (long long)n);
+  if (weighted && !(wsum > 0.0))
+    return fail(c, MIPWA_EINVAL, "the weights must have a positive sum (%g)", wsum);
   smp.sorted = false;
   if (will_sort) {
     // the old sample is no longer needed: it takes the first pass, and the
     // validated copy the final order
     rc = ensure(c, &smp.cur, &smp.cur_cap, bytes);
+    if (!rc && weighted) rc = ensure(c, &smp.w_cur, &smp.w_cur_cap, wbytes);
     if (rc) return rc;
     CK(c, launch_sort_rest(dtype == MIPWA_F32, c->model, smp.spare, n, smp.cur, smp.spare,
-                           c->d_sortwork, c->stream));
+                           c->d_sortwork, c->stream, weighted ? smp.w_spare : nullptr,
+                           weighted ? smp.w_cur : nullptr, weighted ? smp.w_spare : nullptr));
     c->launches += kSortLaunches - 1;
     // no wait: later work on the context stream is ordered after the sort, and
     // the next copy into this sample's spare buffer waits for this event
@@ -441,6 +479,12 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
     std::swap(smp.cur_cap, smp.spare_cap);
     CK(c, cudaEventRecord(smp.spare_free, c->stream));
   }
+  if (weighted) {
+    std::swap(smp.w_cur, smp.w_spare);
+    std::swap(smp.w_cur_cap, smp.w_spare_cap);
+  }
+  smp.weighted = weighted;
+  smp.wsum = weighted ? wsum : (double)n;
   smp.n = n;
   smp.dtype = dtype;
   smp.set = true;
@@ -455,9 +499,13 @@ int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
   const size_t bytes = (size_t)smp.n * ev_bytes(smp.dtype);
   int rc = ensure(c, &smp.spare, &smp.spare_cap, bytes);
   if (!rc) rc = ensure_sortwork(c);
+  if (!rc && smp.weighted)
+    rc = ensure(c, &smp.w_spare, &smp.w_spare_cap,
+                (size_t)smp.n * (smp.dtype == MIPWA_F32 ? sizeof(float) : sizeof(double)));
   if (rc) return rc;
   CK(c, launch_sort(smp.dtype == MIPWA_F32, c->model, smp.cur, smp.n, smp.spare, smp.cur,
-                    c->d_sortwork, c->stream));
+                    c->d_sortwork, c->stream, smp.weighted ? smp.w_cur : nullptr,
+                    smp.weighted ? smp.w_spare : nullptr, smp.weighted ? smp.w_cur : nullptr));
   c->launches += kSortLaunches;
   CK(c, cudaEventRecord(smp.spare_free, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
@@ -485,7 +533,8 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   const bool gram = c->gram_on;
   const int nseg = c->model.kn.n - 1;
   // one block count for nll and nll_grad, so they sum identically
-  const int per_sm = eval_blocks_per_sm(f32, ev32, c->model, c->basis_on);
+  const int per_sm = eval_blocks_per_sm(f32, ev32, c->model, c->basis_on,
+                                        c->norm.weighted && !gram);
   int total = c->sm_count * per_sm;
   const int64_t need_d = (c->data.n + kThreads - 1) / kThreads;
   const int64_t need_n = (c->norm.n + kThreads - 1) / kThreads;
@@ -551,6 +600,8 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   a.basis_data = c->basis_on ? c->data.basis : nullptr;
   a.basis_norm = (c->basis_on && !gram) ? c->norm.basis : nullptr;
   a.model = c->model;
+  a.norm_w = (c->norm.weighted && !gram) ? c->norm.w_cur : nullptr;
+  a.norm_count = c->norm.wsum;
   if (c->timing) CK(c, cudaEventRecord(c->ev0, c->stream));
   if (gram) {
     CK(c, launch_gram_rows(want_grad, f32, c->model, c->d_coef, 0, c->d_gram,
@@ -638,6 +689,8 @@ int evaluate_bw(mipwa_ctx* c, const double* params, double* nll, double* grad,
   a.basis_data = nullptr;
   a.basis_norm = nullptr;
   a.model = c->model;
+  a.norm_w = c->norm.weighted ? c->norm.w_cur : nullptr;
+  a.norm_count = c->norm.wsum;
   CK(c, launch_eval_bw(ev32, a, grid, c->stream));
   c->launches += 2;
   double* h_out = c->h_stage + kParamsMax;
@@ -743,6 +796,8 @@ int enqueue_toys(mipwa_ctx* c, cudaStream_t st) {
   a.basis_data = c->basis_on ? c->toys.basis : nullptr;
   a.basis_norm = (c->basis_on && !c->gram_on) ? c->norm.basis : nullptr;
   a.model = c->model;
+  a.norm_w = (c->norm.weighted && !c->gram_on) ? c->norm.w_cur : nullptr;
+  a.norm_count = c->norm.wsum;
   CK(c, launch_toys(f32, ev32, a, q.grid, st));
   CK(c, cudaMemcpyAsync(q.h_out, q.d_out, (size_t)T * (1 + P) * sizeof(double),
                         cudaMemcpyDeviceToHost, st));
@@ -838,6 +893,7 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
       cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_counter, sizeof(unsigned int)) != cudaSuccess ||
       cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&c->d_wsum, kWeightSumDoubles * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&c->h_stage, kStage * sizeof(double)) != cudaSuccess)
     return bail(MIPWA_ENOMEM);
   if (cudaMemset(c->d_counter, 0, sizeof(unsigned int)) != cudaSuccess) return bail(MIPWA_ECUDA);
@@ -868,7 +924,7 @@ void mipwa_destroy(mipwa_ctx* c) {
                   (void*)c->d_partials, (void*)c->d_sortwork, c->data.basis, c->norm.basis,
                   (void*)c->d_cells, (void*)c->d_gram,
                   c->data.cur, c->data.spare, c->norm.cur,
-                  c->norm.spare})
+                  c->norm.spare, c->norm.w_cur, c->norm.w_spare, (void*)c->d_wsum})
     if (p) cudaFree(p);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   invalidate_graph(c);
@@ -929,6 +985,7 @@ int mipwa_set_masses(mipwa_ctx* c, double mD, double m1, double m2) {
   c->n_params = -1;
   c->data.set = c->norm.set = false;
   c->data.n = c->norm.n = 0;
+  c->norm.weighted = false;
   return MIPWA_OK;
 }
 
@@ -1021,8 +1078,13 @@ int mipwa_set_events(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, int on
 
 int mipwa_set_norm_sample(mipwa_ctx* c, const void* ptr, int64_t n, int dtype, int on_device,
                           int64_t* n_outside) {
+  return mipwa_set_norm_sample_weighted(c, ptr, nullptr, n, dtype, on_device, n_outside);
+}
+
+int mipwa_set_norm_sample_weighted(mipwa_ctx* c, const void* ptr, const void* weights, int64_t n,
+                                   int dtype, int on_device, int64_t* n_outside) {
   if (!c) return MIPWA_EINVAL;
-  const int rc = set_sample(c, c->norm, ptr, n, dtype, on_device, n_outside, false);
+  const int rc = set_sample(c, c->norm, ptr, n, dtype, on_device, n_outside, false, weights);
   if (rc == MIPWA_OK) {
     c->tq.planned = false;
     c->gram_valid = false;

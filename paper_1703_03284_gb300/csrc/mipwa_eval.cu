@@ -420,7 +420,7 @@ __device__ __forceinline__ void flush_bins_warp(EvalSmem<T>& sm, int cur, T (&ac
 template <typename T, bool GRAD, bool BWG = false>
 __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
                               const double* partials, int d0, int dn, int n0, int nn,
-                              int64_t n_data, int64_t n_norm, double* out, int* flags) {
+                              int64_t n_data, double norm_count, double* out, int* flags) {
   const int R = m.n_res, N = m.kn.n, nseg = N - 1;
   const int W0 = partial_width(N, R, GRAD);
   const int W = W0 + (BWG ? 2 * R : 0);
@@ -436,7 +436,7 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
   const double nd = (double)n_data;
   if (threadIdx.x == 0) {
     if (!(S > 0.0) || !isfinite(S)) atomicOr(flags, kFlagIntegral);
-    out[0] = -2.0 * sm.fin_d[0] + 2.0 * nd * log(S / (double)n_norm);
+    out[0] = -2.0 * sm.fin_d[0] + 2.0 * nd * log(S / norm_count);
   }
   if constexpr (GRAD) {
     const double kappa = 2.0 * nd / S;
@@ -494,11 +494,12 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
 // row: [sum ln|A|^2 (data) or sum |A|^2 (normalisation), c_r adjoint (2R),
 // spline polynomial adjoints (8 (N-1))]. The per-evaluation model data must be
 // staged in sm; the bins are zeroed here. Every thread of the block calls this.
-template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false>
+template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false,
+          bool WN = false>
 __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
                                  const Cplx<T>* cached, int64_t n, int64_t first, int64_t end,
                                  int64_t stride, bool is_data, double* row, int* flags,
-                                 const double* coef64) {
+                                 const double* coef64, const void* norm_w = nullptr) {
   static_assert(!BWG || (std::is_same<T, double>::value && GRAD && !CACHED && SIG == 0),
                 "mass/width derivatives: FP64, direct, with the gradient");
   const int R = m.n_res, nseg = m.kn.n - 1;
@@ -578,7 +579,14 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
         }
       } else {
         ok = isfinite(A2);
-        if (ok) sum.add(A2);
+        if (ok) {
+          if constexpr (WN) {  // weighted normalisation: w |A|^2, adjoint weight w
+            wt = (T)reinterpret_cast<const decltype(EvT::x)*>(norm_w)[i];
+            sum.add(wt * A2);
+          } else {
+            sum.add(A2);
+          }
+        }
       }
       bad |= ok ? 0 : 1;
     }
@@ -682,8 +690,10 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   }
 }
 
-// FP32 kernels: at most 64 registers, four 256-thread blocks per SM.
-template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false>
+// FP32 kernels: at most 64 registers, four 256-thread blocks per SM. WN: the
+// normalisation events carry weights (a.norm_w).
+template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false,
+          bool WN = false>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
     eval_kernel(const EvalArgs a) {
   __shared__ EvalSmem<T> sm;
@@ -702,10 +712,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
   const int64_t chunk = ((n + nb - 1) / nb + kThreads - 1) / kThreads * kThreads;
   const int64_t c0 = (int64_t)b * chunk;
   const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
-  accumulate_range<T, EvT, GRAD, SIG, CACHED, BWG>(sm, m, ev, cached, n, c0, c1,
-                                                   (int64_t)kThreads, is_data,
-                                                   a.partials + (size_t)blockIdx.x * W, a.flags,
-                                                   a.coef);
+  accumulate_range<T, EvT, GRAD, SIG, CACHED, BWG, WN>(sm, m, ev, cached, n, c0, c1,
+                                                       (int64_t)kThreads, is_data,
+                                                       a.partials + (size_t)blockIdx.x * W,
+                                                       a.flags, a.coef, a.norm_w);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -716,7 +726,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
   if (!sm.is_last) return;
   __threadfence();
   finalize_rows<T, GRAD, BWG>(sm, m, a.lu, a.partials, 0, a.nb_data, a.nb_data, a.nb_norm,
-                              a.n_data, a.n_norm, a.out, a.flags);
+                              a.n_data, a.norm_count > 0.0 ? a.norm_count : (double)a.n_norm,
+                              a.out, a.flags);
   if (threadIdx.x == 0) *a.counter = 0u;
 }
 
@@ -726,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1)
 // normalisation sample for one toy, and writes one partial row. Items come
 // chunk-major (all toys of a normalisation chunk in turn), so a chunk is read
 // from HBM once and then from L2.
-template <typename T, typename EvT, bool CACHED, int SIG = 0>
+template <typename T, typename EvT, bool CACHED, int SIG = 0, bool WN = false>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) toys_kernel(const ToyArgs a) {
   __shared__ EvalSmem<T> sm;
   __shared__ int item_sh;
@@ -745,10 +756,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 1) toys_kernel(
     const Cplx<T>* cached =
         reinterpret_cast<const Cplx<T>*>(it.is_data ? a.basis_data : a.basis_norm);
     const int64_t n = it.is_data ? a.n_data : a.n_norm;
-    accumulate_range<T, EvT, true, SIG, CACHED>(sm, m, ev, cached, n, it.start, it.end,
-                                                (int64_t)kThreads, it.is_data != 0,
-                                                a.partials + (size_t)it.row * W, a.flags,
-                                                a.coef + (size_t)it.toy * cs);
+    accumulate_range<T, EvT, true, SIG, CACHED, false, WN>(
+        sm, m, ev, cached, n, it.start, it.end, (int64_t)kThreads, it.is_data != 0,
+        a.partials + (size_t)it.row * W, a.flags, a.coef + (size_t)it.toy * cs, a.norm_w);
   }
 }
 
@@ -761,7 +771,8 @@ __global__ void __launch_bounds__(kThreads) toys_finalize_kernel(const ToyArgs a
   const int base = t * a.rows_per_toy;
   const int64_t n_data = a.offsets[t + 1] - a.offsets[t];
   finalize_rows<T, true>(sm, a.model, a.lu, a.partials, base + a.norm_chunks,
-                         a.data_rows[t], base, a.norm_chunks, n_data, a.n_norm,
+                         a.data_rows[t], base, a.norm_chunks, n_data,
+                         a.norm_count > 0.0 ? a.norm_count : (double)a.n_norm,
                          a.out + (size_t)t * (1 + P), a.flags);
 }
 
@@ -823,9 +834,9 @@ __global__ void inside_kernel(const Model m, const EvT* ev, int64_t n, uint8_t* 
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T, typename EvT, bool GRAD, int SIG = 0, bool CACHED = false>
+template <typename T, typename EvT, bool GRAD, int SIG = 0, bool CACHED = false, bool WN = false>
 static cudaError_t run_eval(const EvalArgs& a, int grid, cudaStream_t st) {
-  eval_kernel<T, EvT, GRAD, SIG, CACHED><<<grid, kThreads, 0, st>>>(a);
+  eval_kernel<T, EvT, GRAD, SIG, CACHED, false, WN><<<grid, kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -839,6 +850,12 @@ static int model_sig(const Model& m) {
 template <typename T, typename EvT>
 static cudaError_t dispatch_eval(bool grad, bool cached, int sig, const EvalArgs& a, int grid,
                                  cudaStream_t st) {
+  if (a.norm_w) {  // weighted normalisation: the generic kernels only
+    if (cached) return grad ? run_eval<T, EvT, true, 0, true, true>(a, grid, st)
+                            : run_eval<T, EvT, false, 0, true, true>(a, grid, st);
+    return grad ? run_eval<T, EvT, true, 0, false, true>(a, grid, st)
+                : run_eval<T, EvT, false, 0, false, true>(a, grid, st);
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (cached && sig == kSigPD) return grad ? run_eval<T, EvT, true, kSigPD, true>(a, grid, st)
                                              : run_eval<T, EvT, false, kSigPD, true>(a, grid, st);
@@ -872,8 +889,13 @@ cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& 
 template <typename T, typename EvT>
 static cudaError_t run_toys(bool cached, const ToyArgs& a, int grid, cudaStream_t st) {
   // FP32 with the cached basis: kernels specialised for P+D models
-  const int sig = cached ? model_sig(a.model) : 0;
+  const int sig = cached && !a.norm_w ? model_sig(a.model) : 0;
   bool done = false;
+  if (a.norm_w) {  // weighted normalisation: the generic kernels only
+    if (cached) toys_kernel<T, EvT, true, 0, true><<<grid, kThreads, 0, st>>>(a);
+    else toys_kernel<T, EvT, false, 0, true><<<grid, kThreads, 0, st>>>(a);
+    done = true;
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (sig == kSigPD) {
       toys_kernel<T, EvT, true, kSigPD><<<grid, kThreads, 0, st>>>(a);
@@ -903,8 +925,13 @@ cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int grid,
 }
 
 cudaError_t launch_eval_bw(int ev_f32, const EvalArgs& a, int grid, cudaStream_t st) {
-  if (ev_f32) eval_kernel<double, float2, true, 0, false, true><<<grid, kThreads, 0, st>>>(a);
-  else eval_kernel<double, double2, true, 0, false, true><<<grid, kThreads, 0, st>>>(a);
+  if (a.norm_w) {
+    if (ev_f32) eval_kernel<double, float2, true, 0, false, true, true><<<grid, kThreads, 0, st>>>(a);
+    else eval_kernel<double, double2, true, 0, false, true, true><<<grid, kThreads, 0, st>>>(a);
+  } else {
+    if (ev_f32) eval_kernel<double, float2, true, 0, false, true><<<grid, kThreads, 0, st>>>(a);
+    else eval_kernel<double, double2, true, 0, false, true><<<grid, kThreads, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -987,8 +1014,8 @@ static int occ_pair(bool cached, int sig) {
   return std::min(occ<T, EvT, false>(), occ<T, EvT, true>());
 }
 
-int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached) {
-  const int pd = model_sig(m);
+int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached, bool weighted) {
+  const int pd = weighted ? 0 : model_sig(m);
   if (compute_f32) return ev_f32 ? occ_pair<float, float2>(cached, pd)
                                  : occ_pair<float, double2>(cached, pd);
   return ev_f32 ? occ_pair<double, float2>(cached, pd) : occ_pair<double, double2>(cached, pd);

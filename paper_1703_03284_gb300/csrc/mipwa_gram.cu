@@ -109,8 +109,11 @@ __device__ void moment_desc(int idx, int R, int& i1, int& j1, int& i2, int& j2, 
   }
 }
 
-template <typename EvT, bool F32B>
+// W: each event's products are weighted by its weight (wts, the events'
+// scalar type), kept in the spare last column of V.
+template <typename EvT, bool F32B, bool W>
 __global__ void __launch_bounds__(kGramThreads) gram_build_kernel(const Model m, const EvT* ev,
+                                                                  const void* wts,
                                                                   const int* first,
                                                                   const int* last,
                                                                   double* moments) {
@@ -134,6 +137,7 @@ __global__ void __launch_bounds__(kGramThreads) gram_build_kernel(const Model m,
       const double s12 = (double)e.x, s13 = (double)e.y;
       const double t1 = s12 - knot[j12], t2 = s13 - knot[j13];
       v[0] = 1.0;
+      if constexpr (W) v[kVMax] = (double)reinterpret_cast<const decltype(EvT::x)*>(wts)[i];
       double p1 = 1.0, p2 = 1.0;
 #pragma unroll
       for (int k = 1; k <= 6; ++k) {
@@ -167,7 +171,14 @@ __global__ void __launch_bounds__(kGramThreads) gram_build_kernel(const Model m,
     __syncthreads();
     if ((int)threadIdx.x < M) {
       const int ne = e1 - base < kGramThreads ? e1 - base : kGramThreads;
-      if (s2 == 0.0) {  // one product: all moments but the |B|^2 and conj(B_r) B_s ones
+      if constexpr (W) {
+        if (s2 == 0.0) {
+          for (int k = 0; k < ne; ++k) acc = fma(V[k][kVMax] * V[k][i1], V[k][j1], acc);
+        } else {
+          for (int k = 0; k < ne; ++k)
+            acc = fma(V[k][kVMax], fma(V[k][i1], V[k][j1], s2 * V[k][i2] * V[k][j2]), acc);
+        }
+      } else if (s2 == 0.0) {  // one product: all moments but the |B|^2 and conj(B_r) B_s ones
         for (int k = 0; k < ne; ++k) acc = fma(V[k][i1], V[k][j1], acc);
       } else {
         for (int k = 0; k < ne; ++k) acc = fma(V[k][i1], V[k][j1], fma(s2 * V[k][i2], V[k][j2], acc));
@@ -317,25 +328,35 @@ __global__ void __launch_bounds__(64) gram_rows_kernel(const Model m, const doub
 
 }  // namespace
 
-cudaError_t launch_gram_build(int ev_f32, int compute_f32, const Model& m, const void* ev,
-                              const int* first, const int* last, double* moments,
-                              cudaStream_t st) {
-  const int nkeys = (m.kn.n - 1) * (m.kn.n - 1);
-  if (ev_f32) {
-    if (compute_f32)
-      gram_build_kernel<float2, true><<<nkeys, kGramThreads, 0, st>>>(m, (const float2*)ev, first,
-                                                                     last, moments);
+template <typename EvT>
+static void gram_build(int compute_f32, const Model& m, const EvT* ev, const void* wts,
+                       const int* first, const int* last, double* moments, int nkeys,
+                       cudaStream_t st) {
+  if (compute_f32) {
+    if (wts)
+      gram_build_kernel<EvT, true, true><<<nkeys, kGramThreads, 0, st>>>(m, ev, wts, first, last,
+                                                                         moments);
     else
-      gram_build_kernel<float2, false><<<nkeys, kGramThreads, 0, st>>>(m, (const float2*)ev, first,
-                                                                      last, moments);
+      gram_build_kernel<EvT, true, false><<<nkeys, kGramThreads, 0, st>>>(m, ev, nullptr, first,
+                                                                          last, moments);
   } else {
-    if (compute_f32)
-      gram_build_kernel<double2, true><<<nkeys, kGramThreads, 0, st>>>(m, (const double2*)ev,
-                                                                      first, last, moments);
+    if (wts)
+      gram_build_kernel<EvT, false, true><<<nkeys, kGramThreads, 0, st>>>(m, ev, wts, first, last,
+                                                                          moments);
     else
-      gram_build_kernel<double2, false><<<nkeys, kGramThreads, 0, st>>>(m, (const double2*)ev,
-                                                                       first, last, moments);
+      gram_build_kernel<EvT, false, false><<<nkeys, kGramThreads, 0, st>>>(m, ev, nullptr, first,
+                                                                           last, moments);
   }
+}
+
+cudaError_t launch_gram_build(int ev_f32, int compute_f32, const Model& m, const void* ev,
+                              const void* wts, const int* first, const int* last,
+                              double* moments, cudaStream_t st) {
+  const int nkeys = (m.kn.n - 1) * (m.kn.n - 1);
+  if (ev_f32)
+    gram_build(compute_f32, m, (const float2*)ev, wts, first, last, moments, nkeys, st);
+  else
+    gram_build(compute_f32, m, (const double2*)ev, wts, first, last, moments, nkeys, st);
   return cudaGetLastError();
 }
 

@@ -28,6 +28,10 @@ struct EvalArgs {
   const void* basis_data;    // cached B_r per data event (resonance-major) or null
   const void* basis_norm;    // the same for the normalisation sample; null: compute B_r
   Model model;
+  // weights of the normalisation events (the events' scalar type) or null,
+  // and the normalising count: sum of the weights (0: n_norm)
+  const void* norm_w = nullptr;
+  double norm_count = 0.0;
 };
 
 enum { kFlagData = 1, kFlagNorm = 2, kFlagIntegral = 4 };
@@ -61,6 +65,8 @@ struct ToyArgs {
   const void* basis_data;    // cached basis of the toy events or null
   const void* basis_norm;    // cached basis of the normalisation sample or null
   Model model;
+  const void* norm_w = nullptr;  // as in EvalArgs
+  double norm_count = 0.0;
 };
 
 // Spline setup for n_sets parameter vectors (params[s*P ...]) into
@@ -86,14 +92,18 @@ cudaError_t launch_amp2(int compute_f32, int ev_f32, const Model& m, const doubl
 cudaError_t launch_inside(int ev_f32, const Model& m, const void* ev, int64_t n, uint8_t* out,
                           unsigned long long* n_out, int grid, cudaStream_t stream);
 // Blocks per SM of the event kernel that runs for this model and form.
-int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached);
+int eval_blocks_per_sm(int compute_f32, int ev_f32, const Model& m, bool cached,
+                       bool weighted = false);
 
 // Stable sort of n events from src into dst by spline cell (j12, j13), in two
 // counting passes through tmp (n events; src may equal dst, not tmp); work
-// holds sort_workspace_ints() ints. n must be below 2^31.
+// holds sort_workspace_ints() ints. n must be below 2^31. With wsrc not null,
+// one weight per event (the events' scalar type) moves with it: wsrc -> wtmp
+// -> wdst (the same aliasing rules).
 cudaError_t sort_workspace_ints(int n_knots, size_t* ints);
 cudaError_t launch_sort(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
-                        void* dst, int* work, cudaStream_t stream);
+                        void* dst, int* work, cudaStream_t stream, const void* wsrc = nullptr,
+                        void* wtmp = nullptr, void* wdst = nullptr);
 // The same split at the first count, which also adds the number of events
 // outside the Dalitz plot to *outside (device): validate, then finish with
 // launch_sort_rest (nothing is written before it). The count may run in
@@ -104,7 +114,15 @@ cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* sr
                                       cudaStream_t stream, int piece = 0, int n_pieces = 1);
 int64_t sort_piece_begin(int64_t n, int piece, int n_pieces);
 cudaError_t launch_sort_rest(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
-                             void* dst, int* work, cudaStream_t stream);
+                             void* dst, int* work, cudaStream_t stream,
+                             const void* wsrc = nullptr, void* wtmp = nullptr,
+                             void* wdst = nullptr);
+// Sum of n weights (float if f32, else double) in FP64, in a fixed order:
+// work holds kWeightSumDoubles doubles; on completion work[256] is the sum and
+// the 8 bytes after it count the weights that are not finite.
+constexpr int kWeightSumDoubles = 256 + 2;
+cudaError_t launch_weight_sum(int f32, const void* w, int64_t n, double* work,
+                              cudaStream_t stream);
 // Index range [first[k], last[k]) of every spline cell k = j12 (N-1) + j13 in
 // a sample grouped by cell (n < 2^31); empty cells get [0, 0).
 cudaError_t launch_cell_bounds(int ev_f32, const Knots& kn, const void* ev, int64_t n, int* first,
@@ -112,10 +130,11 @@ cudaError_t launch_cell_bounds(int ev_f32, const Knots& kn, const void* ev, int6
 
 // Re/Im form: per-cell moments (gram_moments(R) doubles per cell, (N-1)^2
 // cells) of a sample grouped by cell: FP64 products and sums; the
-// Breit-Wigner terms in FP64, or in the FP32-mixed form when compute_f32.
+// Breit-Wigner terms in FP64, or in the FP32-mixed form when compute_f32;
+// each event's products weighted by its weight when wts is not null.
 cudaError_t launch_gram_build(int ev_f32, int compute_f32, const Model& m, const void* ev,
-                              const int* first, const int* last, double* moments,
-                              cudaStream_t stream);
+                              const void* wts, const int* first, const int* last,
+                              double* moments, cudaStream_t stream);
 // Re/Im form: the normalisation rows of n_sets parameter sets (coefficients
 // at coef + set * coef_stride, prepare-kernel layout): set s writes rows
 // [s * row_stride, s * row_stride + N - 1) of `rows` in the partial-row layout

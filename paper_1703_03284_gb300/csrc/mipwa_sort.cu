@@ -214,20 +214,27 @@ constexpr int kTileRows = kBatch<EvT>;
 template <typename EvT>
 constexpr int kTile = kScatterThreads * kTileRows<EvT>;
 
+// A weight per event (PAY) travels with it: the events' scalar type.
 template <typename EvT>
+using Scalar = decltype(EvT::x);
+
+template <typename EvT, bool PAY>
 struct ScatterSmem {
   EvT stage[kTile<EvT>];                // the tile in key order
+  Scalar<EvT> wstage[PAY ? kTile<EvT> : 1];  // and the weight of each (PAY)
   unsigned char skey[kTile<EvT>];       // and the key of each
   int whist[kScatterWarps][kMaxKeys];   // per warp: count, then its first tile position
   int delta[kMaxKeys];                  // output position - tile position, per key
   int cursor[kMaxKeys];                 // next output position of each key
 };
 
-// One tile of tn events starting at src (FULL: tn = kTile, no bounds checks).
-template <typename EvT, int DIGIT, bool FULL>
-__device__ __forceinline__ void scatter_tile(ScatterSmem<EvT>& sm, const Knots& kn, int nkeys,
-                                             const EvT* __restrict__ src, int tn,
-                                             EvT* __restrict__ dst) {
+// One tile of tn events starting at src (FULL: tn = kTile, no bounds checks);
+// PAY: their weights from wsrc go to wdst alongside.
+template <typename EvT, int DIGIT, bool FULL, bool PAY>
+__device__ __forceinline__ void scatter_tile(ScatterSmem<EvT, PAY>& sm, const Knots& kn, int nkeys,
+                                             const EvT* __restrict__ src,
+                                             const Scalar<EvT>* __restrict__ wsrc, int tn,
+                                             EvT* __restrict__ dst, Scalar<EvT>* __restrict__ wdst) {
   constexpr int R = kTileRows<EvT>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lane_lt = (1u << lane) - 1u;
@@ -237,10 +244,15 @@ __device__ __forceinline__ void scatter_tile(ScatterSmem<EvT>& sm, const Knots& 
   __syncwarp();
   const int wbase = warp * 32 * R + lane;
   EvT e[R];
+  Scalar<EvT> w[PAY ? R : 1];
   int kr[R];  // the key (bits 0-7), then also the rank (bits 8 and up)
 #pragma unroll
-  for (int u = 0; u < R; ++u)
-    if (FULL || wbase + 32 * u < tn) e[u] = __ldcs(src + wbase + 32 * u);
+  for (int u = 0; u < R; ++u) {
+    if (FULL || wbase + 32 * u < tn) {
+      e[u] = __ldcs(src + wbase + 32 * u);
+      if constexpr (PAY) w[u] = __ldcs(wsrc + wbase + 32 * u);
+    }
+  }
 #pragma unroll
   for (int u = 0; u < R; ++u)
     kr[u] = (FULL || wbase + 32 * u < tn) ? digit_of<EvT, DIGIT>(kn, e[u]) : 0;
@@ -310,20 +322,26 @@ __device__ __forceinline__ void scatter_tile(ScatterSmem<EvT>& sm, const Knots& 
       const int key = kr[u] & 0xff;
       const int p = sm.whist[warp][key] + (kr[u] >> 8);
       sm.stage[p] = e[u];
+      if constexpr (PAY) sm.wstage[p] = w[u];
       sm.skey[p] = (unsigned char)key;
     }
   }
   __syncthreads();  // barrier 3: the tile is in key order
-  for (int j = threadIdx.x; j < (FULL ? kTile<EvT> : tn); j += kScatterThreads)
-    dst[sm.delta[sm.skey[j]] + j] = sm.stage[j];
+  for (int j = threadIdx.x; j < (FULL ? kTile<EvT> : tn); j += kScatterThreads) {
+    const int pos = sm.delta[sm.skey[j]] + j;
+    dst[pos] = sm.stage[j];
+    if constexpr (PAY) wdst[pos] = sm.wstage[j];
+  }
 }
 
-template <typename EvT, int DIGIT>
+template <typename EvT, int DIGIT, bool PAY>
 __global__ void __launch_bounds__(kScatterThreads, 3)
-    sort_scatter_kernel(const Knots kn, const EvT* __restrict__ src, int64_t n,
-                        const int* __restrict__ offsets, EvT* __restrict__ dst) {
+    sort_scatter_kernel(const Knots kn, const EvT* __restrict__ src,
+                        const Scalar<EvT>* __restrict__ wsrc, int64_t n,
+                        const int* __restrict__ offsets, EvT* __restrict__ dst,
+                        Scalar<EvT>* __restrict__ wdst) {
   constexpr int T = kTile<EvT>;
-  __shared__ ScatterSmem<EvT> sm;
+  __shared__ ScatterSmem<EvT, PAY> sm;
   const int nkeys = kn.n - 1;
   if (threadIdx.x < nkeys)
     sm.cursor[threadIdx.x] = offsets[(size_t)blockIdx.x * nkeys + threadIdx.x];
@@ -331,9 +349,68 @@ __global__ void __launch_bounds__(kScatterThreads, 3)
   const int64_t b0 = chunk_begin(n, blockIdx.x), b1 = chunk_begin(n, blockIdx.x + 1);
   const int len = (int)(b1 - b0);
   src += b0;
+  if constexpr (PAY) wsrc += b0;
   int t0 = 0;
-  for (; t0 + T <= len; t0 += T) scatter_tile<EvT, DIGIT, true>(sm, kn, nkeys, src + t0, T, dst);
-  if (t0 < len) scatter_tile<EvT, DIGIT, false>(sm, kn, nkeys, src + t0, len - t0, dst);
+  for (; t0 + T <= len; t0 += T)
+    scatter_tile<EvT, DIGIT, true, PAY>(sm, kn, nkeys, src + t0, PAY ? wsrc + t0 : nullptr, T, dst,
+                                        wdst);
+  if (t0 < len)
+    scatter_tile<EvT, DIGIT, false, PAY>(sm, kn, nkeys, src + t0, PAY ? wsrc + t0 : nullptr,
+                                         len - t0, dst, wdst);
+}
+
+// ------------------------------------------------------------ sample weights
+// The sum of a sample's weights in FP64, in an order fixed by n alone (so it is
+// the same on every call), and the number of weights that are not finite.
+constexpr int kWsumBlocks = 256;
+
+template <typename W>
+__global__ void __launch_bounds__(256)
+    weight_partial_kernel(const W* __restrict__ w, int64_t n, double* part,
+                          unsigned long long* bad) {
+  __shared__ double red[256];
+  const int64_t per = (n + kWsumBlocks - 1) / kWsumBlocks;
+  const int64_t b0 = per * blockIdx.x < n ? per * blockIdx.x : n;
+  const int64_t b1 = b0 + per < n ? b0 + per : n;
+  double s = 0.0;
+  unsigned int nb = 0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += 256) {
+    const double x = (double)w[i];
+    if (isfinite(x)) s += x;
+    else ++nb;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+  for (int off = 16; off > 0; off >>= 1) nb += __shfl_down_sync(0xffffffffu, nb, off);
+  if ((threadIdx.x & 31) == 0 && nb) atomicAdd(bad, (unsigned long long)nb);
+}
+
+__global__ void __launch_bounds__(256) weight_final_kernel(const double* part, double* out) {
+  __shared__ double red[256];
+  red[threadIdx.x] = part[threadIdx.x];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+cudaError_t launch_weight_sum(int f32, const void* w, int64_t n, double* work, cudaStream_t st) {
+  unsigned long long* bad = (unsigned long long*)(work + kWsumBlocks + 1);
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (f32)
+    weight_partial_kernel<float><<<kWsumBlocks, 256, 0, st>>>((const float*)w, n, work, bad);
+  else
+    weight_partial_kernel<double><<<kWsumBlocks, 256, 0, st>>>((const double*)w, n, work, bad);
+  weight_final_kernel<<<1, 256, 0, st>>>(work, work + kWsumBlocks);
+  return cudaGetLastError();
 }
 
 // first[k], last[k] = the index range of key k in a sample grouped by key
@@ -382,10 +459,11 @@ static cudaError_t count_pass(const Model& m, const EvT* src, int64_t n, int* wo
   return cudaGetLastError();
 }
 
-// Offsets and scatter of one pass whose counts are in `work`.
+// Offsets and scatter of one pass whose counts are in `work` (with the
+// events' weights from wsrc to wdst when wsrc is not null).
 template <typename EvT, int DIGIT>
 static cudaError_t finish_pass(const Knots& kn, const EvT* src, int64_t n, EvT* dst, int* work,
-                               cudaStream_t st) {
+                               cudaStream_t st, const Scalar<EvT>* wsrc, Scalar<EvT>* wdst) {
   const int nkeys = kn.n - 1;
   int* group_sum = work + (size_t)nkeys * kSortBlocks;
   int* key_start = group_sum + (size_t)nkeys * kGroups;
@@ -393,17 +471,27 @@ static cudaError_t finish_pass(const Knots& kn, const EvT* src, int64_t n, EvT* 
   sort_group_sums<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum);
   sort_key_starts<<<1, 1024, 0, st>>>(group_sum, nkeys, key_start);
   sort_offsets<<<cgrid, 256, 0, st>>>(work, nkeys, group_sum, key_start);
-  sort_scatter_kernel<EvT, DIGIT><<<kSortBlocks, kScatterThreads, 0, st>>>(kn, src, n, work, dst);
+  if (wsrc)
+    sort_scatter_kernel<EvT, DIGIT, true>
+        <<<kSortBlocks, kScatterThreads, 0, st>>>(kn, src, wsrc, n, work, dst, wdst);
+  else
+    sort_scatter_kernel<EvT, DIGIT, false>
+        <<<kSortBlocks, kScatterThreads, 0, st>>>(kn, src, nullptr, n, work, dst, nullptr);
   return cudaGetLastError();
 }
 
 // Both passes after the first count: src -> tmp by j13, tmp -> dst by j12.
 template <typename EvT>
 static cudaError_t sort_rest(const Model& m, const EvT* src, int64_t n, EvT* tmp, EvT* dst,
-                             int* work, cudaStream_t st) {
-  cudaError_t e = finish_pass<EvT, kFirstDigit>(m.kn, src, n, tmp, work, st);
+                             int* work, cudaStream_t st, const void* wsrc, void* wtmp,
+                             void* wdst) {
+  using W = Scalar<EvT>;
+  cudaError_t e = finish_pass<EvT, kFirstDigit>(m.kn, src, n, tmp, work, st, (const W*)wsrc,
+                                                (W*)wtmp);
   if (e == cudaSuccess) e = count_pass<EvT, kSecondDigit, false>(m, tmp, n, work, nullptr, st);
-  if (e == cudaSuccess) e = finish_pass<EvT, kSecondDigit>(m.kn, tmp, n, dst, work, st);
+  if (e == cudaSuccess)
+    e = finish_pass<EvT, kSecondDigit>(m.kn, tmp, n, dst, work, st,
+                                       wsrc ? (const W*)wtmp : nullptr, (W*)wdst);
   return e;
 }
 
@@ -423,21 +511,25 @@ int64_t sort_piece_begin(int64_t n, int piece, int n_pieces) {
 }
 
 cudaError_t launch_sort_rest(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
-                             void* dst, int* work, cudaStream_t st) {
+                             void* dst, int* work, cudaStream_t st, const void* wsrc, void* wtmp,
+                             void* wdst) {
   if (ev_f32)
-    return sort_rest(m, (const float2*)src, n, (float2*)tmp, (float2*)dst, work, st);
-  return sort_rest(m, (const double2*)src, n, (double2*)tmp, (double2*)dst, work, st);
+    return sort_rest(m, (const float2*)src, n, (float2*)tmp, (float2*)dst, work, st, wsrc, wtmp,
+                     wdst);
+  return sort_rest(m, (const double2*)src, n, (double2*)tmp, (double2*)dst, work, st, wsrc, wtmp,
+                   wdst);
 }
 
 cudaError_t launch_sort(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
-                        void* dst, int* work, cudaStream_t st) {
+                        void* dst, int* work, cudaStream_t st, const void* wsrc, void* wtmp,
+                        void* wdst) {
   cudaError_t e;
   if (ev_f32)
     e = count_pass<float2, kFirstDigit, false>(m, (const float2*)src, n, work, nullptr, st);
   else
     e = count_pass<double2, kFirstDigit, false>(m, (const double2*)src, n, work, nullptr, st);
   if (e != cudaSuccess) return e;
-  return launch_sort_rest(ev_f32, m, src, n, tmp, dst, work, st);
+  return launch_sort_rest(ev_f32, m, src, n, tmp, dst, work, st, wsrc, wtmp, wdst);
 }
 
 }  // namespace mipwa
