@@ -83,7 +83,7 @@ def parse():
                     help="data events (= normalisation events)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--nll-steps", type=int, default=50, help="NLL-only (no gradient) steps")
-    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cached-steps", type=int, default=10)
     ap.add_argument("--toys-steps", type=int, default=3)
     ap.add_argument("--reim-steps", type=int, default=10)
