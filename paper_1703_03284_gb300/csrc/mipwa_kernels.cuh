@@ -107,8 +107,9 @@ cudaError_t launch_sort(int ev_f32, const Model& m, const void* src, int64_t n, 
 // The same split at the first count, which also adds the number of events
 // outside the Dalitz plot to *outside (device): validate, then finish with
 // launch_sort_rest (nothing is written before it). The count may run in
-// n_pieces (a power of two up to 64) launches, piece p reading only the events
-// [sort_piece_begin(n, p, n_pieces), sort_piece_begin(n, p + 1, n_pieces)).
+// n_pieces (1 to 8) launches, piece p reading only the events
+// [sort_piece_begin(n, p, n_pieces), sort_piece_begin(n, p + 1, n_pieces)):
+// halving pieces, the last two equal (1/2, 1/4, ..., 1/128, 1/128 for 8).
 cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* src, int64_t n,
                                       int* work, unsigned long long* outside,
                                       cudaStream_t stream, int piece = 0, int n_pieces = 1);

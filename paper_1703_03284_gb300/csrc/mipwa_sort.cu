@@ -29,7 +29,7 @@
 
 namespace mipwa {
 
-constexpr int kSortBlocks = 152 * 32;  // chunks; a multiple of kGroup and of 64 pieces
+constexpr int kSortBlocks = 152 * 32;  // chunks; a multiple of kGroup and of 2^7
 constexpr int kMaxKeys = 64;           // keys of one pass: N-1 segments
 static_assert(kMaxKnots - 1 <= kMaxKeys, "a pass key must fit the tables");
 
@@ -495,10 +495,19 @@ static cudaError_t sort_rest(const Model& m, const EvT* src, int64_t n, EvT* tmp
   return e;
 }
 
+// First chunk of piece p of n_pieces (p = n_pieces: the end): halving pieces,
+// 1/2, 1/4, ... of the chunks, the last two equal, so that the piece whose
+// count waits for the whole copy is the smallest.
+static int piece_chunk(int p, int n_pieces) {
+  if (p <= 0) return 0;
+  if (p >= n_pieces) return kSortBlocks;
+  return kSortBlocks - (kSortBlocks >> p);
+}
+
 cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* src, int64_t n,
                                       int* work, unsigned long long* outside, cudaStream_t st,
                                       int piece, int n_pieces) {
-  const int c0 = kSortBlocks / n_pieces * piece, c1 = kSortBlocks / n_pieces * (piece + 1);
+  const int c0 = piece_chunk(piece, n_pieces), c1 = piece_chunk(piece + 1, n_pieces);
   if (ev_f32)
     return count_pass<float2, kFirstDigit, true>(m, (const float2*)src, n, work, outside, st, c0,
                                                  c1);
@@ -507,7 +516,7 @@ cudaError_t launch_sort_count_checked(int ev_f32, const Model& m, const void* sr
 }
 
 int64_t sort_piece_begin(int64_t n, int piece, int n_pieces) {
-  return chunk_begin(n, kSortBlocks / n_pieces * piece);
+  return chunk_begin(n, piece_chunk(piece, n_pieces));
 }
 
 cudaError_t launch_sort_rest(int ev_f32, const Model& m, const void* src, int64_t n, void* tmp,
