@@ -123,7 +123,9 @@ namespace {
 // results [NLL, gradient (P), resonance derivatives (2R)], then the flags.
 constexpr int kParamsMax = 2 * kMaxRes + 2 * kMaxKnots;
 constexpr int kOutMax = 1 + kParamsMax + 2 * kMaxRes;
-constexpr int kStage = kParamsMax + kOutMax + 1;
+// pinned staging: parameters, results (+ flags), then set_sample's read-backs
+constexpr int kSetBack = kParamsMax + kOutMax + 1;  // outside count, weight sum, bad weights
+constexpr int kStage = kSetBack + 3;
 
 int fail(mipwa_ctx* c, int code, const char* fmt, ...) {
   if (c) {
@@ -386,8 +388,12 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
     if (rc) return rc;
   }
   const bool will_sort = c->have_model && sortable(n) && !smp.no_sort;
-  unsigned long long outside = 0, wbad = 0;
-  double wsum = 0.0;
+  // read back through pinned memory (outside count, weight sum, bad weights)
+  unsigned long long* h_outside = reinterpret_cast<unsigned long long*>(c->h_stage + kSetBack);
+  double* h_wsum = c->h_stage + kSetBack + 1;
+  unsigned long long* h_wbad = reinterpret_cast<unsigned long long*>(c->h_stage + kSetBack + 2);
+  *h_outside = *h_wbad = 0;
+  *h_wsum = 0.0;
   if (n > 0) {
     if (on_device) {
       if (!is_device_ptr(ptr))
@@ -439,15 +445,17 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
                             c->stream));
       CK(c, launch_weight_sum(dtype == MIPWA_F32, smp.w_spare, n, c->d_wsum, c->stream));
       c->launches += 2;
-      CK(c, cudaMemcpyAsync(&wsum, c->d_wsum + 256, sizeof(double), cudaMemcpyDeviceToHost,
+      CK(c, cudaMemcpyAsync(h_wsum, c->d_wsum + 256, sizeof(double), cudaMemcpyDeviceToHost,
                             c->stream));
-      CK(c, cudaMemcpyAsync(&wbad, c->d_wsum + 257, sizeof(wbad), cudaMemcpyDeviceToHost,
-                            c->stream));
+      CK(c, cudaMemcpyAsync(h_wbad, c->d_wsum + 257, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, c->stream));
     }
-    CK(c, cudaMemcpyAsync(&outside, c->d_count, sizeof(outside), cudaMemcpyDeviceToHost,
-                          c->stream));
+    CK(c, cudaMemcpyAsync(h_outside, c->d_count, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
   }
+  const unsigned long long outside = *h_outside, wbad = *h_wbad;
+  const double wsum = *h_wsum;
   if (outside > 0) {
     if (n_outside) *n_outside = (int64_t)outside;
     return fail(c, MIPWA_EOUTSIDE, "%llu of %lld events lie outside the Dalitz plot", outside,
