@@ -306,12 +306,13 @@ __device__ __forceinline__ void bin_add(EvalSmem<T>& sm, int idx, T v) {
 // polynomial bins: d|A|^2/d a(s) = 2 Re(A* e^{i phi}) and
 // d|A|^2/d phi(s) = 2 a Re(A* i e^{i phi}) (Re/Im form: d|A|^2/dx(s) = 2 Re A,
 // d|A|^2/dy(s) = 2 Im A), times t^m, t = s - s_j (the exact knot: the FP32
-// form evaluates about float(s_j) and shifts back here).
+// form evaluates about float(s_j) and shifts back here). Aw = 2 wt A: the
+// event's weight and the factor 2 applied once.
 template <typename T>
 __device__ __forceinline__ void swave_adjoint(const EvalSmem<T>& sm, const SwavePart<T>& w,
-                                              bool reim, Cplx<T> A, T wt, T* v) {
-  const T abar = reim ? T(2) * wt * A.re : T(2) * wt * (A.re * w.cs + A.im * w.sn);
-  const T pbar = reim ? T(2) * wt * A.im : T(2) * wt * w.a * (A.im * w.cs - A.re * w.sn);
+                                              bool reim, Cplx<T> Aw, T* v) {
+  const T abar = reim ? Aw.re : Aw.re * w.cs + Aw.im * w.sn;
+  const T pbar = reim ? Aw.im : w.a * (Aw.im * w.cs - Aw.re * w.sn);
   T t1 = w.t;
   if constexpr (std::is_same<T, float>::value) t1 = w.t - sm.knot_lo[w.j];
   const T t2 = t1 * t1, t3 = t2 * t1;
@@ -593,12 +594,13 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
     if constexpr (GRAD) {
       T v[16];
       if (ok) {
+        const Cplx<T> Aw{T(2) * wt * A.re, T(2) * wt * A.im};  // d(wt |A|^2)/dA*
         constexpr int NRg = sig_spins(SIG) ? sig_count(sig_spins(SIG)) : kMaxRes;
 #pragma unroll
         for (int r = 0; r < NRg; ++r) {
           if (sig_spins(SIG) || r < R) {
-            gc[2 * r] += T(2) * wt * (A.re * B[r].re + A.im * B[r].im);
-            gc[2 * r + 1] += T(2) * wt * (A.im * B[r].re - A.re * B[r].im);
+            gc[2 * r] += Aw.re * B[r].re + Aw.im * B[r].im;
+            gc[2 * r + 1] += Aw.im * B[r].re - Aw.re * B[r].im;
           }
         }
         if constexpr (BWG) {
@@ -609,14 +611,14 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
               const double cr = sm.cre[r], ci = sm.cim[r];
               const double xm = cr * dBm[r].re - ci * dBm[r].im, ym = cr * dBm[r].im + ci * dBm[r].re;
               const double xw = cr * dBw[r].re - ci * dBw[r].im, yw = cr * dBw[r].im + ci * dBw[r].re;
-              gb[2 * r] += 2.0 * wt * (A.re * xm + A.im * ym);
-              gb[2 * r + 1] += 2.0 * wt * (A.re * xw + A.im * yw);
+              gb[2 * r] += Aw.re * xm + Aw.im * ym;
+              gb[2 * r + 1] += Aw.re * xw + Aw.im * yw;
             }
           }
         }
         const bool reim = SIG == 0 ? m.reim != 0 : sig_reim(SIG);
-        swave_adjoint(sm, sw.c12, reim, A, wt, v);
-        swave_adjoint(sm, sw.c13, reim, A, wt, v + 8);
+        swave_adjoint(sm, sw.c12, reim, Aw, v);
+        swave_adjoint(sm, sw.c13, reim, Aw, v + 8);
       } else {
 #pragma unroll
         for (int k = 0; k < 16; ++k) v[k] = T(0);
