@@ -297,7 +297,8 @@ int mipwa_kernel_time(mipwa_ctx* ctx, double* ms, int64_t* n_launches);
  * or MIPWA_EOUTSIDE), params as P host doubles, and the result is written to
  * the DEVICE buffer d_out (at least 1 + P doubles). Work is queued on
  * `stream` (NULL: legacy default stream); the call blocks until it is done.
- * Events are used in the caller's order (not regrouped by spline cell).
+ * Events are used in the caller's order (not regrouped by spline cell), and
+ * every normalisation point has weight 1 (no weighted samples here).
  *
  * It calls no allocator: every intermediate buffer lives in one fixed
  * file-scope device array of about 2.5 MB (at most 608 blocks, N <= 64 knots,

@@ -8,8 +8,9 @@
 //
 // A least-significant-digit sort with the segment indices as digits: a stable
 // counting pass by j13, then a stable counting pass by j12, which leaves the
-// events in the order of the cell key j12 (N-1) + j13 with equal keys in the
-// order given (deterministic for a given input). Each pass has N-1 <= 63 keys:
+// events in the order of the cell key j12 (N-1) + j13, events with equal keys
+// in the order they had before (deterministic for a given input). Each pass
+// has N-1 <= 63 keys:
 //   1. count:   a thread block counts the keys of one contiguous chunk into
 //               the chunk's row of a [chunk][key] table (the first pass of a
 //               new sample also counts the events outside the Dalitz plot);
