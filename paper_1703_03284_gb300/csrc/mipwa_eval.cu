@@ -526,8 +526,10 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   // and a thread's consecutive events are 256 apart); every kRegIters
   // iterations the warp adds its sums to the shared bins (one reduce-scatter
   // when the warp shares the cell), and a lane whose cell changes adds its own.
+  // (Measured on the 40-knot workload: 64 iterations, once per flush of the
+  // shared bins to FP64, 0.8 % faster than 16.)
   constexpr bool kThreadBins = std::is_same<T, float>::value;
-  constexpr int kRegIters = 16;
+  constexpr int kRegIters = kFlushIters;
   T acc[16];
   int cur = -1;
   int reg_iter = 0;
