@@ -282,9 +282,12 @@ def _fp32_nll_check(name, n, tol):
         v, g = lik.nll_grad(p)
         vr, gr = P.oracle_for(name).nll_grad(p, d64, n64)
         assert abs(v - vr) < tol, (v, vr)
-        # FP32 gradient: ~1e-5 relative away from the minimum (data events near
-        # zeros of A carry weights 1/|A|^2 on an amplitude with FP32 error),
-        # ~3e-6 at the truth; the fit test bounds its effect on the minimum
+        # FP32 gradient, measured at 1e7 + 1e7 events: ~5e-8 relative at the
+        # perturbed point; ~1.2e-5 at the truth, near the minimum, where the
+        # gradient is small and the FP32 rounding of the large per-cell adjoint
+        # sums dominates (repeated calls differ by up to ~1e-5 there: the
+        # shared-memory bins add in arrival order). The fit test bounds the
+        # effect on the fitted parameters.
         assert grad_rel(g, gr) < 2e-5
         assert abs(lik.nll(p) - v) < 1e-3
 
