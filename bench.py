@@ -67,10 +67,10 @@ def _measured_hbm_gbs() -> float:
 
 HBM_GBS = _measured_hbm_gbs()
 # DRAM bytes (read + write) of the fused FP32 NLL+gradient kernel per event
-# processed, from one ncu capture on 2e7 + 2e7 events (324.92 MB per launch,
+# processed, from one ncu capture on 2e7 + 2e7 events (324.31 MB per launch,
 # profiles/eval_kernel_f32_grad_pipipi_n40.md); a launch's traffic is this
 # times its events. None once the kernel has changed since the capture.
-TRAFFIC_PER_EVENT = 324.92e6 / 4e7
+TRAFFIC_PER_EVENT = 324.31e6 / 4e7
 
 
 def parse():
