@@ -41,20 +41,24 @@ def workload_name(n):
         return WORKLOAD
     return WORKLOAD.replace("1e8", f"{n:.0e}".replace("+0", "").replace("+", ""))
 
-# Algorithmic work per event of one NLL+gradient evaluation of this model
-# (2 resonances, one P- and one D-wave; add/sub/mul = 1, fused multiply-add = 2,
-# each division, square root, sine, cosine and log = 1). Forward: kinematics 24,
-# Zemach 18, Breit-Wigner terms 86, Bose combination 20, S-wave 42, |A|^2 and
-# reduction 5; gradient: c_r 20, spline adjoint 50, weights 1.5.
-FLOPS_PER_EVENT_FWD = 195
-FLOPS_PER_EVENT_GRAD = 267
-# Peaks from unit counts and the maximum SM clock (2070 MHz, 152 SMs):
-#   FP32: 128 lanes x 2 flop x 152 x 2.07 GHz;  FP64: 1.25 TFLOP/s (GB300 nominal).
+# Algorithmic work per event (flops; add/sub/mul/div/sqrt/sin/cos/log = 1
+# each): the FP64 oracle's own formulas instantiated on an operation-counting
+# scalar type (oracle_count_flops), counting the operations that depend on the
+# event once each, on this model at these parameters, averaged over PDF-drawn
+# data and uniform normalisation events in equal numbers (a test recounts
+# them). FWD: -2 ln L only; GRAD: with the gradient's per-event part (weighted
+# adjoint, coefficient sums, segment bins); CACHED: the Breit-Wigner basis read
+# instead of computed; REIM: the Re/Im S-wave form.
+FLOPS_PER_EVENT_FWD = 260.0
+FLOPS_PER_EVENT_GRAD = 353.0
+FLOPS_PER_EVENT_GRAD_CACHED = 179.0
+FLOPS_PER_EVENT_GRAD_REIM = 331.0
+FLOPS_PER_EVENT_GRAD_REIM_CACHED = 157.0
+# Peaks from unit counts and the maximum SM clock (2070 MHz, 152 SMs), for
+# context beside the measured ones: FP32 128 lanes x 2 flop x 152 x 2.07 GHz;
+# FP64 1.25 TFLOP/s (GB300 nominal).
 PEAK_FP32_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25
-# Cached basis: the Breit-Wigner part (kinematics 24, Zemach 18, BW terms 86,
-# symmetrisation 4 flops) is read from memory instead.
-FLOPS_PER_EVENT_GRAD_CACHED = FLOPS_PER_EVENT_GRAD - 132
 
 
 def _measured_hbm_gbs() -> float:
@@ -67,10 +71,10 @@ def _measured_hbm_gbs() -> float:
 
 HBM_GBS = _measured_hbm_gbs()
 # DRAM bytes (read + write) of the fused FP32 NLL+gradient kernel per event
-# processed, from one ncu capture on 2e7 + 2e7 events (324.31 MB per launch,
-# profiles/eval_kernel_f32_grad_pipipi_n40.md); a launch's traffic is this
-# times its events. None once the kernel has changed since the capture.
-TRAFFIC_PER_EVENT = 324.31e6 / 4e7
+# processed, from one ncu capture on 2e7 + 2e7 events (324.31 MB per launch);
+# a launch's traffic is this times its events. None once the kernel has
+# changed since the capture.
+TRAFFIC_PER_EVENT = None
 
 
 def parse():
@@ -97,13 +101,13 @@ def parse():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi every 200 ms in a child process; a reader thread stamps each
+    """nvidia-smi every 50 ms in a child process; a reader thread stamps each
     sample on arrival, and stop() keeps the samples that arrived between
     begin() and end() (plus one sampling period), i.e. during the timed loop."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-    PERIOD_S = 0.2
+    PERIOD_S = 0.05
 
     def __init__(self, gpu: int):
         self.gpu = gpu
@@ -199,6 +203,39 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def bench_config(n: int, world: int) -> dict:
+    """The workload of one step (the same dict for both arms)."""
+    return {"workload": workload_name(n), "n_data": n, "n_norm": n,
+            "l2": (f"inputs ({16 * n / 1e9:.2g} GB) larger than L2 (129 MB); no flush needed"
+                   if 16 * n > 129e6 else "inputs fit in L2 (129 MB): not a valid bench size"),
+            "parallelism": f"replicas x{world} (no collective)"}
+
+
+# ------------------------------------------------------------- ALU peaks
+def probe_peaks(local: int) -> dict:
+    """The library's throughput probes (mipwa_probe_peak) on this GPU: FP32
+    FMA (scalar and packed f32x2), FP64 FMA and the special-function unit,
+    each timed with CUDA events for about 200 ms, with the SM clocks sampled
+    during the probes."""
+    from paper_1703_03284_gb300.api import probe_peak
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.begin()
+    out = {}
+    for kind in ("ffma", "ffma2", "dfma", "mufu"):
+        probe_peak(kind, local, 20.0)  # warm-up
+        ops, ms = probe_peak(kind, local, 200.0)
+        out[kind] = {"ops_per_s": ops, "ms": ms,
+                     "unit": "approximations/s" if kind == "mufu" else "flop/s"}
+    clocks.end()
+    out["clocks"] = clocks.stop()
+    out["fp32_tflops"] = max(out["ffma"]["ops_per_s"], out["ffma2"]["ops_per_s"]) / 1e12
+    out["fp64_tflops"] = out["dfma"]["ops_per_s"] / 1e12
+    out["note"] = ("grid of SMs x 4 blocks x 256 threads, 8 independent chains per thread; "
+                   "fma = 2 flops, packed f32x2 fma = 4")
+    return out
+
+
 # ------------------------------------------------------------- CPU oracle
 def oracle_sample(spec, n: int, seed: int):
     """Data and normalisation samples drawn with the oracle's own density."""
@@ -217,23 +254,53 @@ def oracle_sample(spec, n: int, seed: int):
     return o, data, norm
 
 
-def cpu_baseline(spec, params, n: int = 200_000, target_s: float = 10.0):
-    """The oracle, as it stands, on a bounded sample: repeated NLL+grad
-    evaluations of n + n events for about target_s seconds."""
-    o, data, norm = oracle_sample(spec, n, seed=101)
-    cores = os.cpu_count() or 1
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _time_oracle(o, params, data, norm, threads, target_s):
     t0 = time.perf_counter()
-    o.nll_grad(params, data, norm, threads=cores)
+    o.nll_grad(params, data, norm, threads=threads)
     once = time.perf_counter() - t0
     reps = max(1, min(50, int(target_s / max(once, 1e-3))))
     t0 = time.perf_counter()
     for _ in range(reps):
-        o.nll_grad(params, data, norm, threads=cores)
-    dt = time.perf_counter() - t0
+        o.nll_grad(params, data, norm, threads=threads)
+    return reps, time.perf_counter() - t0
+
+
+def cpu_baseline(spec, params, n: int = 200_000, target_s: float = 10.0):
+    """The oracle, as it stands, on a bounded sample: repeated NLL+grad
+    evaluations of n + n events for about target_s seconds on all host cores,
+    then one thread on a tenth of the sample."""
+    o, data, norm = oracle_sample(spec, n, seed=101)
+    cores = os.cpu_count() or 1
+    reps, dt = _time_oracle(o, params, data, norm, cores, target_s)
+    n1 = n // 10
+    reps1, dt1 = _time_oracle(o, params, data[:n1], norm[:n1], 1, target_s / 2)
     base = {"value": reps * 2 * n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{n} data + {n} normalisation events of the same model (float32-rounded, "
                       f"drawn with the oracle's density), {reps} NLL+grad evaluation(s), "
-                      f"{cores} OpenMP threads"}
+                      f"{cores} OpenMP threads",
+            "single_thread": {"value": reps1 * 2 * n1 / dt1, "unit": "events/s", "cores": 1,
+                              "sample": f"{n1} data + {n1} normalisation events of the same "
+                                        f"sample, {reps1} NLL+grad evaluation(s), 1 thread"}}
     return base, accuracy_vs_oracle(spec, params, o, data, norm, cores)
 
 
@@ -247,8 +314,12 @@ def accuracy_vs_oracle(spec, params, o, data, norm, cores):
     from paper_1703_03284_gb300 import F32, F64, Likelihood
 
     vr, gr = o.nll_grad(params, data, norm, threads=cores)
-    a2r = o.amp2(params, norm)
-    out = {"n_data": len(data), "n_norm": len(norm), "oracle_nll": vr}
+    a2r = {"data": o.amp2(params, data), "uniform": o.amp2(params, norm)}
+    out = {"n_data": len(data), "n_norm": len(norm), "oracle_nll": vr,
+           "amp2_note": ("per-event |A|^2 error on data events (drawn from the PDF; the 1e-5 "
+                         "relative bar) and on uniform normalisation events (near zeros of A "
+                         "the relative error grows as 1/|A|; bar: 1e-5 relative + 1e-8 of the "
+                         "mean |A|^2, at most 0.1% of events above 1e-5 relative)")}
     for mode, name in ((F64, "fp64"), (F32, "fp32_mixed")):
         dt = torch.float32 if mode == F32 else torch.float64
         d = torch.from_numpy(data).to("cuda", dt)
@@ -258,13 +329,18 @@ def accuracy_vs_oracle(spec, params, o, data, norm, cores):
         lik.set_events(d)
         lik.set_norm_sample(nm)
         v, g = lik.nll_grad(params)
-        a2 = lik.amp2(params, nm).cpu().numpy()
-        rel = np.abs(a2 / a2r - 1.0)
-        out[name] = {"nll_abs_err": abs(v - vr), "nll_rel_err": abs(v - vr) / abs(vr),
-                     "grad_rel_err": float(np.linalg.norm(g - gr) / np.linalg.norm(gr)),
-                     "amp2_rel_err_median": float(np.median(rel)),
-                     "amp2_rel_err_max": float(rel.max()),
-                     "amp2_frac_above_1e-5": float(np.mean(rel > 1e-5))}
+        res = {"nll_abs_err": abs(v - vr), "nll_rel_err": abs(v - vr) / abs(vr),
+               "grad_rel_err": float(np.linalg.norm(g - gr) / np.linalg.norm(gr))}
+        for kind, ev in (("data", d), ("uniform", nm)):
+            a2 = lik.amp2(params, ev).cpu().numpy()
+            ref = a2r[kind]
+            rel = np.abs(a2 / ref - 1.0)
+            res[f"amp2_{kind}"] = {
+                "rel_err_median": float(np.median(rel)), "rel_err_max": float(rel.max()),
+                "frac_above_1e-5": float(np.mean(rel > 1e-5)),
+                "max_err_over_bound": float(np.max(np.abs(a2 - ref) /
+                                                   (1e-5 * ref + 1e-8 * ref.mean())))}
+        out[name] = res
     return out
 
 
@@ -291,7 +367,7 @@ def run_reference(args, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
+        "config": bench_config(args.n_events, args.gpus),
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
@@ -329,7 +405,9 @@ def toys_leg(args, stream, rank):
     lik.set_norm_sample(norm)
     lik.set_toys(pool, offsets)
     lik.enable_basis_cache(True)
+    t_tune = time.perf_counter()
     best = lik.toys_autotune(params)
+    t_tune = time.perf_counter() - t_tune
     lik.nll_grad_toys(params)
     launches0 = lik.launch_count()
     torch.cuda.synchronize()
@@ -388,7 +466,7 @@ def toys_leg(args, stream, rank):
             "norm_events": args.toys_norm, "ms_per_iteration": t_ms,
             "toys_per_s": 1e3 * args.n_toys / t_ms,
             "event_pairs_per_s": pairs / (t_ms / 1e3),
-            "autotuned_norm_chunk": best,
+            "autotuned": dict(best, seconds=t_tune),
             "gpu_launches_per_iteration": launches_it,
             "loop_single_toy": loop,
             "speedup_vs_fp64_loop": (1e3 * args.n_toys / t_ms) / loop["fp64"]["toys_per_s"],
@@ -574,12 +652,18 @@ def run(args, world, rank, local, stream):
     value = world * events * args.steps / (t_ms / 1e3)
     k_s = kms / kn / 1e3
     achieved = FLOPS_PER_EVENT_GRAD * events / k_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
+    # ---- the pipes' own peaks on this GPU (after the timed loop)
+    peaks = probe_peaks(local)
+    peak32, peak64 = peaks["fp32_tflops"], peaks["fp64_tflops"]
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak32,
+                "unit": "TFLOP/s", "frac": achieved / peak32,
                 "traffic": None if TRAFFIC_PER_EVENT is None else TRAFFIC_PER_EVENT * events,
                 "kernel": "eval_kernel<float,float2,grad>",
-                "kernel_ms": kms / kn,
-                "peak_note": "FP32 from unit counts x 2070 MHz (nominal, not measured)"}
+                "kernel_ms": kms / kn, "flops_per_event": FLOPS_PER_EVENT_GRAD,
+                "events_per_launch": events,
+                "peak_note": ("of measured: FP32 FMA throughput of this GPU in this run "
+                              "(mipwa_probe_peak, the larger of fma.rn.f32 and fma.rn.f32x2)"),
+                "peak_nominal": PEAK_FP32_TFLOPS, "frac_of_nominal": achieved / PEAK_FP32_TFLOPS}
 
     # ---- NLL alone (no gradient), FP32-mixed, same events
     nll_only = None
@@ -634,10 +718,12 @@ def run(args, world, rank, local, stream):
         ach64 = FLOPS_PER_EVENT_GRAD * events / (kms64 / kn64 / 1e3) / 1e12
         fp64 = {"value": world * events * args.fp64_steps / (t64 / 1e3), "unit": "events/s",
                 "ms_per_step": t64 / args.fp64_steps, "steps": args.fp64_steps,
-                "roofline": {"bound": "alu", "achieved": ach64, "peak": PEAK_FP64_TFLOPS,
-                             "unit": "TFLOP/s", "frac": ach64 / PEAK_FP64_TFLOPS,
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64,
+                             "unit": "TFLOP/s", "frac": ach64 / peak64,
                              "traffic": None, "kernel": "eval_kernel<double,float2,grad>",
-                             "peak_note": "GB300 nominal FP64, not measured"},
+                             "peak_note": "of measured: fma.rn.f64 throughput (mipwa_probe_peak)",
+                             "peak_nominal": PEAK_FP64_TFLOPS,
+                             "frac_of_nominal": ach64 / PEAK_FP64_TFLOPS},
                 "with_bw_mass_width_derivatives": {
                     "ms_per_step": tbw, "value": world * events / (tbw / 1e3), "unit": "events/s",
                     "note": "NLL + gradient + d/d(m_r, Gamma_r) of both resonances, FP64"}}
@@ -667,8 +753,8 @@ def run(args, world, rank, local, stream):
         cached = {"value": world * events * args.cached_steps / (tc / 1e3), "unit": "events/s",
                   "ms_per_step": tc / args.cached_steps, "steps": args.cached_steps,
                   "bytes_per_event": bytes_ev,
-                  "roofline": {"bound": "alu", "achieved": achc, "peak": PEAK_FP32_TFLOPS,
-                               "unit": "TFLOP/s", "frac": achc / PEAK_FP32_TFLOPS,
+                  "roofline": {"bound": "alu", "achieved": achc, "peak": peak32,
+                               "unit": "TFLOP/s", "frac": achc / peak32,
                                "hbm_gbs": hbm, "hbm_frac_of_measured": hbm / HBM_GBS,
                                "traffic": None,
                                "kernel": "eval_kernel<float,float2,grad,cached>"}}
@@ -750,11 +836,8 @@ def run(args, world, rank, local, stream):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": workload_name(n), "n_data": n, "n_norm": n,
-                       "l2": (f"inputs ({16 * n / 1e9:.2g} GB) larger than L2 (129 MB); no flush needed"
-                              if 16 * n > 129e6 else "inputs fit in L2 (129 MB): not a valid bench size"),
-                       "parallelism": f"replicas x{world} (no collective)"},
-            "roofline": roofline, "nll_only": nll_only, "fp64_plain": fp64,
+            "config": bench_config(n, world),
+            "roofline": roofline, "alu_peaks": peaks, "nll_only": nll_only, "fp64_plain": fp64,
             "fp32_cached_basis": cached,
             "batched_toys": toys, "reim_moment_normalisation": reim,
             "paper_workload_fit": paper, "e2e": e2e,

@@ -71,7 +71,7 @@ typedef enum {
   MIPWA_EOUTSIDE = -2, /* an event lies outside the Dalitz plot; nothing stored */
   MIPWA_ENONPOS = -3,  /* |A|^2 <= 0 or non-finite for a data event, or I <= 0 */
   MIPWA_ECUDA = -4,    /* a CUDA runtime call failed (message in last_error) */
-  MIPWA_ETIMEOUT = -5, /* a bounded device wait gave up */
+  MIPWA_ETIMEOUT = -5, /* reserved: no call returns it (no kernel here waits on the device) */
   MIPWA_ESTATE = -6,   /* call order: model / events / normalisation not set */
   MIPWA_ENOMEM = -7    /* device or pinned host allocation failed */
 } mipwa_status;
@@ -240,14 +240,49 @@ int mipwa_set_toys(mipwa_ctx* ctx, const void* s12s13, int64_t n_total, int dtyp
  * nll: n_toys; grad: n_toys * P. Blocks until done. */
 int mipwa_nll_grad_toys(mipwa_ctx* ctx, const double* params, double* nll, double* grad);
 
-/* Time the batched evaluation at `params` for normalisation chunk sizes of
- * 65536 ... 2097152 events per work item and keep the fastest (written to
- * *best_chunk if not NULL). */
-int mipwa_toys_autotune(mipwa_ctx* ctx, const double* params, int64_t* best_chunk);
+/* Launch configuration of the batched evaluation. */
+typedef struct {
+  int64_t norm_chunk; /* normalisation events per work item (default 131072) */
+  int64_t data_chunk; /* at most this many events of one toy per work item (65536) */
+  int block;          /* threads per block of the persistent kernel: 128, 256 (default)
+                         or 512; a weighted normalisation sample takes 256 only */
+  int blocks_per_sm;  /* resident blocks per SM of the persistent grid (0, the
+                         default: as many as fit) */
+} mipwa_toys_config;
+
+/* Set the launch configuration: a zero chunk or block keeps the current value
+ * (blocks_per_sm is always taken). Chunks must be in 256 .. 2^30, block 128,
+ * 256 or 512, blocks_per_sm in 0..16 (MIPWA_EINVAL). Every configuration sums
+ * the same events in other groupings, so results change by rounding only.
+ * Takes effect at the next batched evaluation (work list and graph rebuilt). */
+int mipwa_set_toys_config(mipwa_ctx* ctx, const mipwa_toys_config* cfg);
+int mipwa_get_toys_config(mipwa_ctx* ctx, mipwa_toys_config* cfg);
+
+/* Autotuner of the batched evaluation: times it at `params` (n_toys * P host
+ * doubles) over the launch configurations (a coordinate search: normalisation
+ * chunk 65536 ... 2097152 events, data chunk 32768 ... 262144, block 128 /
+ * 256 / 512, blocks per SM 1 ... as many as fit, then the normalisation chunk
+ * again; configurations with the same work list as a smaller one skipped),
+ * keeps the fastest and writes it to *best (if not NULL). The choice is cached
+ * on the context under a key of the model signature (resonance spins, knot
+ * count and spacing, S-wave form, cached basis, moment normalisation,
+ * weights), compute mode, event dtype, sample sizes and SM count; a later call
+ * with the same key applies the cached choice without timing, as it does for
+ * a key found in the tune file (mipwa_set_toys_tune_file). *n_timed (if not
+ * NULL) receives the number of configurations timed (0: cached choice). */
+int mipwa_toys_autotune(mipwa_ctx* ctx, const double* params, mipwa_toys_config* best,
+                        int* n_timed);
+
+/* A text file of autotuner choices, one "key norm_chunk data_chunk block
+ * blocks_per_sm" line each: mipwa_toys_autotune looks a key up there (the last
+ * matching line wins) and appends each new choice. NULL or "" turns it off. */
+int mipwa_set_toys_tune_file(mipwa_ctx* ctx, const char* path);
 
 /* Capture the batched evaluation in a CUDA graph (on != 0, the default) or
  * launch its kernels one by one. */
 int mipwa_set_toys_graph(mipwa_ctx* ctx, int on);
+
+
 
 /* |A(s12,s13)|^2 at `params` for n events at the DEVICE pointer `d_s12s13`
  * (type dtype), written as doubles to the DEVICE pointer `d_out`; events
@@ -295,7 +330,9 @@ int mipwa_kernel_time(mipwa_ctx* ctx, double* ms, int64_t* n_launches);
  * set_model), the events as DEVICE pointers (d_data: n_data >= 0 pairs,
  * d_norm: n_norm >= 1 pairs, both of type `dtype`, all inside the Dalitz plot
  * or MIPWA_EOUTSIDE), params as P host doubles, and the result is written to
- * the DEVICE buffer d_out (at least 1 + P doubles). Work is queued on
+ * the DEVICE buffer d_out (at least 1 + P doubles). d_data, d_norm and d_out
+ * must be memory of `device` (or managed memory): the kernels dereference
+ * them, so a buffer of another GPU is MIPWA_EINVAL. Work is queued on
  * `stream` (NULL: legacy default stream); the call blocks until it is done.
  * Events are used in the caller's order (not regrouped by spline cell), and
  * every normalisation point has weight 1 (no weighted samples here).
@@ -308,13 +345,29 @@ int mipwa_kernel_time(mipwa_ctx* ctx, double* ms, int64_t* n_launches);
  * that overlap on the GPU (other host threads, other streams) race; the
  * counters that must start at zero are cleared on every call. Returns
  * MIPWA_EINVAL for sizes beyond these limits or bad arguments, MIPWA_ENONPOS
- * when |A|^2 <= 0 for a data event or the integral is not positive, and
+ * when |A|^2 <= 0 for a data event, the integral is not positive or the
+ * NLL written to d_out[0] is not finite (as mipwa_nll_grad), and
  * MIPWA_ECUDA (with a line on stderr) if a CUDA call fails. */
 int mipwa_nll_grad_noalloc(int device, int compute_mode, double mD, double m1, double m2,
                            const mipwa_resonance* res, int n_res, const double* knots,
                            int n_knots, double r_res, double r_D, const void* d_data,
                            int64_t n_data, const void* d_norm, int64_t n_norm, int dtype,
                            const double* params, double* d_out, void* stream);
+
+/* Measured throughput of one arithmetic pipe of the device (the peaks that
+ * roofline fractions of the likelihood kernels are quoted against; the paper
+ * has no counterpart): a grid of SMs x 4 blocks x 256 threads, each thread
+ * running 8 independent chains of one instruction kind, timed with CUDA
+ * events on the legacy default stream for about target_ms (0 < target_ms <=
+ * 10000) after calibration. *ops_per_s receives operations per second: flops
+ * for the FMA kinds (one fma = 2, one packed f32x2 fma = 4), approximations per
+ * second for MIPWA_PROBE_MUFU; *ms (if not NULL) the timed launch's duration.
+ * Allocates and frees a small device buffer. Blocks. */
+#define MIPWA_PROBE_FFMA 0  /* fma.rn.f32 */
+#define MIPWA_PROBE_FFMA2 1 /* fma.rn.f32x2 (two lanes per instruction) */
+#define MIPWA_PROBE_DFMA 2  /* fma.rn.f64 */
+#define MIPWA_PROBE_MUFU 3  /* rsqrt.approx.ftz.f32 (special-function unit) */
+int mipwa_probe_peak(int device, int kind, double target_ms, double* ops_per_s, double* ms);
 
 /* One-line description of the last failure on this context ("" if none). */
 const char* mipwa_last_error(const mipwa_ctx* ctx);

@@ -92,8 +92,11 @@ def _load():
             lib.oracle_nll_grad.argtypes = [pm, pd, i64, pd, i64, pd, pd, pd, i32]
             lib.oracle_nll_grad_w.argtypes = [pm, pd, i64, pd, i64, pd, pd, pd, pd, i32]
             lib.oracle_nll.argtypes = [pm, pd, i64, pd, i64, pd, pd, i32]
+            lib.oracle_count_flops.argtypes = [pm, pd, i64, pd, i32, i32, i32, pd]
+            lib.oracle_nll_grad_local.argtypes = [pm, pd, i64, pd, i64, pd, pd, pd, pd, i32]
             for f in ("oracle_inside", "oracle_amp", "oracle_basis", "oracle_density",
-                      "oracle_nll_grad", "oracle_nll_grad_w", "oracle_nll"):
+                      "oracle_nll_grad", "oracle_nll_grad_w", "oracle_nll",
+                      "oracle_count_flops", "oracle_nll_grad_local"):
                 getattr(lib, f).restype = i32
             _lib = lib
     return _lib
@@ -247,6 +250,36 @@ class Oracle:
         if rc != OK:
             raise ArithmeticError(f"oracle_nll_grad failed ({rc})")
         return out.value, g
+
+
+    def nll_grad_local(self, params, data, norm, threads: int | None = None,
+                       norm_weights=None):
+        """-2 ln L and its gradient with the spline part of the gradient summed
+        in the local (segment-bin) form and mapped to the knots once."""
+        p = self._params(params)
+        d = _events(data) if len(data) else np.zeros((0, 2))
+        n = _events(norm)
+        w = None if norm_weights is None else np.ascontiguousarray(norm_weights, dtype=np.float64)
+        out = ctypes.c_double()
+        g = np.empty(self.n_params)
+        rc = self.lib.oracle_nll_grad_local(ctypes.byref(self.m), _pd(p), len(d), _pd(d), len(n),
+                                            _pd(n), _pd(w) if w is not None else None,
+                                            ctypes.byref(out), _pd(g),
+                                            threads or default_threads())
+        if rc != OK:
+            raise ArithmeticError(f"oracle_nll_grad_local failed ({rc})")
+        return out.value, g
+
+    def count_flops(self, params, events, is_data: bool, grad: bool, cached: bool = False) -> dict:
+        """Mean event-dependent operations per event of one evaluation (see
+        oracle_count_flops): adds, muls, divs, sqrts, funcs and their total."""
+        p, ev = self._params(params), _events(events)
+        out = np.zeros(6)
+        rc = self.lib.oracle_count_flops(ctypes.byref(self.m), _pd(p), len(ev), _pd(ev),
+                                         int(is_data), int(grad), int(cached), _pd(out))
+        if rc != OK:
+            raise ValueError(f"oracle_count_flops failed ({rc})")
+        return dict(zip(("add", "mul", "div", "sqrt", "func", "total"), out.tolist()))
 
 
 def spline_second_derivs(x, y) -> np.ndarray:

@@ -18,6 +18,7 @@ SAMPLE_DATA, SAMPLE_NORM = 0, 1
 MAX_RES = 4
 MAX_KNOTS = 64
 MAX_TOYS = 4096
+PROBE_FFMA, PROBE_FFMA2, PROBE_DFMA, PROBE_MUFU = 0, 1, 2, 3
 
 STATUS_NAMES = {OK: "MIPWA_OK", EINVAL: "MIPWA_EINVAL", EOUTSIDE: "MIPWA_EOUTSIDE",
                 ENONPOS: "MIPWA_ENONPOS", ECUDA: "MIPWA_ECUDA", ETIMEOUT: "MIPWA_ETIMEOUT",
@@ -26,6 +27,12 @@ STATUS_NAMES = {OK: "MIPWA_OK", EINVAL: "MIPWA_EINVAL", EOUTSIDE: "MIPWA_EOUTSID
 
 class Resonance(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("width", ctypes.c_double), ("spin", ctypes.c_int)]
+
+
+class ToysConfig(ctypes.Structure):
+    """Mirror of ``mipwa_toys_config``."""
+    _fields_ = [("norm_chunk", ctypes.c_int64), ("data_chunk", ctypes.c_int64),
+                ("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
 
 
 # (name, restype, argtypes) of every exported function
@@ -52,8 +59,12 @@ SIGNATURES = [
     ("mipwa_nll_grad", _i, [_vp, _pd, _pd, _pd]),
     ("mipwa_set_toys", _i, [_vp, _vp, _i64, _i, _i, _pi64, _i, _pi64]),
     ("mipwa_nll_grad_toys", _i, [_vp, _pd, _pd, _pd]),
-    ("mipwa_toys_autotune", _i, [_vp, _pd, _pi64]),
+    ("mipwa_toys_autotune", _i, [_vp, _pd, ctypes.POINTER(ToysConfig), ctypes.POINTER(_i)]),
     ("mipwa_set_toys_graph", _i, [_vp, _i]),
+    ("mipwa_set_toys_config", _i, [_vp, ctypes.POINTER(ToysConfig)]),
+    ("mipwa_get_toys_config", _i, [_vp, ctypes.POINTER(ToysConfig)]),
+    ("mipwa_set_toys_tune_file", _i, [_vp, ctypes.c_char_p]),
+    ("mipwa_probe_peak", _i, [_i, _i, _d, _pd, _pd]),
     ("mipwa_amp2", _i, [_vp, _pd, _vp, _i64, _i, _vp]),
     ("mipwa_inside", _i, [_vp, _vp, _i64, _i, _vp]),
     ("mipwa_get_sample", _i, [_vp, _i, _vp, _i64, _pi64, ctypes.POINTER(_i)]),

@@ -8,12 +8,18 @@ pointers, everything else as host pointers.
 from __future__ import annotations
 
 import ctypes
+import os
 from typing import Sequence
 
 import numpy as np
 
 from . import _lib
 from ._lib import F32, F64
+
+
+def _config_dict(cfg) -> dict:
+    return {"norm_chunk": cfg.norm_chunk, "data_chunk": cfg.data_chunk, "block": cfg.block,
+            "blocks_per_sm": cfg.blocks_per_sm}
 
 
 class MipwaError(RuntimeError):
@@ -211,16 +217,39 @@ class Likelihood:
                                                   nll.ctypes.data_as(pd), g.ctypes.data_as(pd)))
         return nll, g
 
-    def toys_autotune(self, params) -> int:
+    def toys_autotune(self, params) -> dict:
+        """Time the batched evaluation over its launch configurations, keep the
+        fastest; returns it as a dict with "n_timed" (0: a cached choice)."""
         self._follow_stream()
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
-        best = ctypes.c_int64(0)
+        cfg = _lib.ToysConfig()
+        n_timed = ctypes.c_int(0)
         self._check(self._lib.mipwa_toys_autotune(
-            self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(best)))
-        return best.value
+            self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cfg),
+            ctypes.byref(n_timed)))
+        out = _config_dict(cfg)
+        out["n_timed"] = n_timed.value
+        return out
 
     def set_toys_graph(self, on: bool = True):
         self._check(self._lib.mipwa_set_toys_graph(self._h, int(bool(on))))
+
+    def set_toys_config(self, norm_chunk: int = 0, data_chunk: int = 0, block: int = 0,
+                        blocks_per_sm: int = 0):
+        """Launch configuration of the batched evaluation (0 keeps a chunk or
+        the block size; blocks_per_sm 0 = as many as fit)."""
+        cfg = _lib.ToysConfig(int(norm_chunk), int(data_chunk), int(block), int(blocks_per_sm))
+        self._check(self._lib.mipwa_set_toys_config(self._h, ctypes.byref(cfg)))
+
+    def toys_config(self) -> dict:
+        cfg = _lib.ToysConfig()
+        self._check(self._lib.mipwa_get_toys_config(self._h, ctypes.byref(cfg)))
+        return _config_dict(cfg)
+
+    def set_toys_tune_file(self, path):
+        """File of autotuner choices (looked up, then appended to); None: off."""
+        arg = None if path is None else os.fsencode(path)
+        self._check(self._lib.mipwa_set_toys_tune_file(self._h, arg))
 
     def num_params(self) -> int:
         return int(self._lib.mipwa_num_params(self._h))
@@ -327,15 +356,36 @@ class Likelihood:
         return int(self._lib.mipwa_launch_count(self._h))
 
 
-def nll_grad_noalloc(spec, params, data, norm, compute_mode: int = F64, device: int = 0):
+PROBES = {"ffma": _lib.PROBE_FFMA, "ffma2": _lib.PROBE_FFMA2, "dfma": _lib.PROBE_DFMA,
+          "mufu": _lib.PROBE_MUFU}
+
+
+def probe_peak(kind: str, device: int = 0, target_ms: float = 100.0) -> tuple[float, float]:
+    """mipwa_probe_peak: (operations per second, timed milliseconds) of one
+    pipe ("ffma", "ffma2", "dfma" in flops/s; "mufu" in approximations/s)."""
+    lib = _lib.load()
+    ops = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    rc = lib.mipwa_probe_peak(int(device), PROBES[kind], float(target_ms), ctypes.byref(ops),
+                              ctypes.byref(ms))
+    if rc != _lib.OK:
+        raise MipwaError(rc, f"mipwa_probe_peak({kind}) failed")
+    return ops.value, ms.value
+
+
+def nll_grad_noalloc(spec, params, data, norm, compute_mode: int = F64):
     """mipwa_nll_grad_noalloc through the C ABI: no context and no device
     allocation inside the library. `data` and `norm` are CUDA tensors (n, 2) of
-    one dtype; returns (NLL, gradient) read back from a caller-owned buffer."""
+    one dtype on one device, which is the device the call runs on; returns
+    (NLL, gradient) read back from a caller-owned buffer."""
     import torch
     lib = _lib.load()
     if not (isinstance(data, torch.Tensor) and data.is_cuda and isinstance(norm, torch.Tensor)
             and norm.is_cuda and data.dtype == norm.dtype):
         raise ValueError("data and norm must be CUDA tensors of one dtype")
+    if data.device != norm.device:
+        raise ValueError("data and norm must be on the same device")
+    device = data.device.index if data.device.index is not None else torch.cuda.current_device()
     d_ptr, nd, code, _, kd = _event_buffer(data)
     n_ptr, nn, code_n, _, kn = _event_buffer(norm)
     res = (_lib.Resonance * max(len(spec.resonances), 1))()

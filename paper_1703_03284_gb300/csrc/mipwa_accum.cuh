@@ -1,0 +1,702 @@
+// Device building blocks of the fused MIPWA likelihood kernels (sm_103a):
+// shared-memory layout, per-event amplitude (Eq. 1, Bose-symmetrised as in
+// Sec. 4), adjoint of |A|^2, per-block accumulation of one event range into a
+// partial row, and the fixed-order final reduction. Included by the event
+// kernels (mipwa_eval.cu) and the batched-toys kernels (mipwa_toys.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "mipwa_amp.cuh"
+#include "mipwa_kernels.cuh"
+#include "mipwa_pair.cuh"
+
+namespace mipwa {
+
+
+// Compile-time model signature of the FP32 kernels: 0 = read the resonance
+// count and spins from the model at run time; otherwise one decimal digit per
+// resonance, digit = L + 1 (23: a P-wave and a D-wave).
+__host__ __device__ constexpr int sig_count(int sig) {
+  int n = 0;
+  for (; sig > 0; sig /= 10) ++n;
+  return n;
+}
+// spin of resonance r (digit r counted from the most significant one)
+__host__ __device__ constexpr int sig_L(int sig, int r) {
+  for (int k = sig_count(sig) - 1 - r; k > 0; --k) sig /= 10;
+  return sig % 10 - 1;
+}
+constexpr int kSigPD = 23;
+static_assert(sig_count(kSigPD) == 2 && sig_L(kSigPD, 0) == 1 && sig_L(kSigPD, 1) == 2, "sig");
+// A signature plus kSigReim: the same spins with the Re/Im S-wave form.
+constexpr int kSigReim = 1000;
+constexpr int kSigPDReim = kSigReim + kSigPD;
+__host__ __device__ constexpr int sig_spins(int sig) { return sig % kSigReim; }
+__host__ __device__ constexpr bool sig_reim(int sig) { return sig >= kSigReim; }
+
+// Per-thread running sums: plain FP64, or Kahan-compensated FP32.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Shared memory of the event kernels: the model's per-evaluation data (form
+// dependent) plus the reduction scratch.
+struct SmemCommon {
+  float binf[kMaxSeg * 8];    // FP32 form: bins of the current flush window
+  double bind[kMaxSeg * 8];   // FP64 bins of the polynomial adjoints
+  double red[kMaxBlock / 32][1 + 4 * kMaxRes];
+  double fin_d[1 + 4 * kMaxRes + 8 * kMaxSeg];
+  double fin_n[1 + 4 * kMaxRes + 8 * kMaxSeg];
+  double ybar[2][kMaxKnots];
+  double mbar[2][kMaxKnots];
+  int is_last;
+};
+
+template <typename T>
+struct EvalSmem;
+template <>
+struct EvalSmem<double> : SmemCommon {
+  double coef[kMaxSeg * 8];  // magnitude and phase cubics, about s_j
+  double knot[kMaxKnots];
+  double cre[kMaxRes], cim[kMaxRes];
+};
+template <>
+struct EvalSmem<float> : SmemCommon {
+  __align__(16) float coef[kMaxSeg * kSeg32];  // hi/lo cubics about float(s_j), e^{i phi_ref}
+  float knot[kMaxKnots];     // float(s_j)
+  float knot_lo[kMaxKnots];  // s_j - float(s_j)
+  float cre[kMaxRes], cre_lo[kMaxRes], cim[kMaxRes], cim_lo[kMaxRes];
+};
+
+struct EvalCoefs {
+  const double* coef;   // FP64 form
+  const float* coef32;  // FP32 form
+};
+
+__device__ inline void stage(EvalSmem<double>& sm, const Model& m, const EvalCoefs& cf) {
+  const int nseg = m.kn.n - 1;
+  for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) sm.coef[i] = cf.coef[i];
+  for (int i = threadIdx.x; i < m.kn.n; i += blockDim.x) sm.knot[i] = m.kn.s[i];
+  if (threadIdx.x < m.n_res) {
+    sm.cre[threadIdx.x] = cf.coef[nseg * 8 + 2 * threadIdx.x];
+    sm.cim[threadIdx.x] = cf.coef[nseg * 8 + 2 * threadIdx.x + 1];
+  }
+}
+
+__device__ inline void stage(EvalSmem<float>& sm, const Model& m, const EvalCoefs& cf) {
+  const int nseg = m.kn.n - 1;
+  for (int i = threadIdx.x; i < nseg * kSeg32; i += blockDim.x) sm.coef[i] = cf.coef32[i];
+  for (int i = threadIdx.x; i < m.kn.n; i += blockDim.x) {
+    const float hi = (float)m.kn.s[i];
+    sm.knot[i] = hi;
+    sm.knot_lo[i] = (float)(m.kn.s[i] - (double)hi);
+  }
+  if (threadIdx.x < m.n_res) {
+    const float* c = cf.coef32 + nseg * kSeg32 + 4 * threadIdx.x;
+    sm.cre[threadIdx.x] = c[0];
+    sm.cre_lo[threadIdx.x] = c[1];
+    sm.cim[threadIdx.x] = c[2];
+    sm.cim_lo[threadIdx.x] = c[3];
+  }
+}
+
+// S-wave pieces of one channel kept for the adjoint.
+template <typename T>
+struct SwavePart {
+  int j;
+  T t, a, cs, sn;
+};
+
+// The S-wave pieces of both channels.
+template <typename T>
+struct SwaveState {
+  SwavePart<T> c12, c13;
+  __device__ int j12() const { return c12.j; }
+  __device__ int j13() const { return c13.j; }
+};
+
+// ---------------------------------------------------------------- FP64 form
+// A = sum_r c_r B_r
+template <int NR>
+__device__ __forceinline__ Cplx<double> combine(const Model& m, const EvalSmem<double>& sm,
+                                                const Cplx<double>* B) {
+  Cplx<double> A{0.0, 0.0};
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r < m.n_res) {
+      A.re += sm.cre[r] * B[r].re - sm.cim[r] * B[r].im;
+      A.im += sm.cre[r] * B[r].im + sm.cim[r] * B[r].re;
+    }
+  }
+  return A;
+}
+
+// A += a(s) e^{i phi(s)} for one channel (Re/Im form: A += x(s) + i y(s)).
+__device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<double>& sm, double s,
+                                          bool reim, SwavePart<double>& w, Cplx<double>& A) {
+  w.j = segment_of(m.kn, sm.knot, s);
+  w.t = s - sm.knot[w.j];
+  const double* a = &sm.coef[w.j * 8];
+  w.a = ((a[3] * w.t + a[2]) * w.t + a[1]) * w.t + a[0];
+  const double ph = ((a[7] * w.t + a[6]) * w.t + a[5]) * w.t + a[4];
+  if (reim) {
+    A.re += w.a;
+    A.im += ph;
+    return;
+  }
+  sincos(ph, &w.sn, &w.cs);
+  A.re += w.a * w.cs;
+  A.im += w.a * w.sn;
+}
+
+// ---------------------------------------------------------------- FP32 form
+// FP32 form: cubic value as an exact pair hi + lo: the hi-coefficient Horner
+// tail t (a1 + a2 t + a3 t^2) plus a0 by TwoSum, the lo-coefficient Horner
+// added to the low part.
+__device__ __forceinline__ F2 cubic_hl(const float4 hi, const float4 lo, float t) {
+  const float tq = fmaf(fmaf(hi.w, t, hi.z), t, hi.y) * t;
+  const float pl = fmaf(fmaf(fmaf(lo.w, t, lo.z), t, lo.y), t, lo.x);
+  F2 v = two_sum(hi.x, tq);
+  v.lo += pl;
+  return v;
+}
+
+// B_r / cscale_r for the FP32 form (SIG: compile-time resonance spins, or 0),
+// both channels in the two lanes of packed pairs.
+template <int SIG>
+__device__ __forceinline__ void bw_basis(const Model& m, float s12, float s13, Cplx<float>* B) {
+  const ConstsF& c = m.cf;
+  const ChanP k = channel_p(c, P2{s12, s13});
+  F2P z1;
+  P2 z2;
+  zemach_p(c, k, P2{s13, s12}, z1, z2);
+  constexpr int SP = sig_spins(SIG);
+  constexpr int NR = SP ? sig_count(SP) : kMaxRes;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (SP || r < m.n_res) {
+      const int L = SP ? sig_L(SP, r) : c.L[r];
+      const CplxP u = bw_p(c, r, L, k, z1, z2);
+      B[r].re = u.re.x + u.re.y;
+      B[r].im = u.im.x + u.im.y;
+    }
+  }
+}
+
+template <int NR>
+__device__ __forceinline__ Cplx<float> combine(const Model& m, const EvalSmem<float>& sm,
+                                               const Cplx<float>* B) {
+  Cplx<float> A{0.0f, 0.0f};
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r < m.n_res) {
+      A.re += mul_hl(sm.cre[r], sm.cre_lo[r], B[r].re) - mul_hl(sm.cim[r], sm.cim_lo[r], B[r].im);
+      A.im += mul_hl(sm.cre[r], sm.cre_lo[r], B[r].im) + mul_hl(sm.cim[r], sm.cim_lo[r], B[r].re);
+    }
+  }
+  return A;
+}
+
+// sin and cos of a small phase |d| <= kSmallPhase: Taylor series through d^9
+// and d^8 (truncation below 5e-12 there), the leading coefficients -1/6 and
+// 1/24 as float pairs (the same rounding rules as sincos_cw).
+__device__ __forceinline__ void sincos_small(float d, float* sn, float* cs) {
+  const float s = d * d;
+  float ps = fmaf(s, 2.7557318844628753e-06f, -1.9841270113829523e-04f);
+  ps = fmaf(s, ps, 8.333333767950535e-03f);
+  ps = fmaf(s, ps, 4.967053879312289e-09f) + -0.1666666716337204f;
+  *sn = fmaf(d * s, ps, d);
+  float pc = fmaf(s, 2.4801587642286904e-05f, -1.3888889225199819e-03f);
+  pc = fmaf(s, pc, -1.2417634698280722e-09f) + 0.0416666679084301f;
+  *cs = fmaf(s, fmaf(s, pc, -0.5f), 1.0f);
+}
+
+__device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<float>& sm, float s,
+                                          bool reim, SwavePart<float>& w, Cplx<float>& A) {
+  w.j = segment_of(m.kn, sm.knot, s);
+  w.t = __fsub_rn(s, sm.knot[w.j]);  // exact (Sterbenz) on the knot grids used here
+  const float* seg = &sm.coef[w.j * kSeg32];
+  const float4* c4 = reinterpret_cast<const float4*>(seg);
+  const F2 a = cubic_hl(c4[0], c4[1], w.t);
+  if (reim) {
+    const F2 ph = cubic_hl(c4[2], c4[3], w.t);
+    A.re += a.hi + a.lo;
+    A.im += ph.hi + ph.lo;
+    return;
+  }
+  if (seg[20] != 0.0f) {
+    // e^{i phi} = e^{i phi_ref} e^{i delta}, delta = phi - phi_ref (the phase
+    // cubic without its hi constant term; small over this segment)
+    const float4 h = c4[2], l = c4[3], e = c4[4];  // e: cos phi_ref hi/lo, sin phi_ref hi/lo
+    const float tq = fmaf(fmaf(h.w, w.t, h.z), w.t, h.y) * w.t;
+    const float pl = fmaf(fmaf(fmaf(l.w, w.t, l.z), w.t, l.y), w.t, l.x);
+    float sd, cd;
+    sincos_small(tq + pl, &sd, &cd);
+    w.cs = fmaf(e.x, cd, fmaf(e.y, cd, -fmaf(e.z, sd, e.w * sd)));
+    w.sn = fmaf(e.z, cd, fmaf(e.w, cd, fmaf(e.x, sd, e.y * sd)));
+  } else {
+    const F2 ph = cubic_hl(c4[2], c4[3], w.t);
+    sincos_cw(ph.hi, ph.lo, &w.sn, &w.cs);
+  }
+  w.a = a.hi;
+  A.re += mul_hl(a.hi, a.lo, w.cs);
+  A.im += mul_hl(a.hi, a.lo, w.sn);
+}
+
+// ------------------------------------------------------ whole amplitude
+// Forward amplitude of one event: fills the Bose-symmetrised Breit-Wigner
+// basis B[r] (FP32 form: B_r / cscale_r) and the S-wave pieces of both
+// channels. With a cached basis, B is read instead of computed.
+template <typename T, int SIG, bool CACHED>
+__device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& sm, T s12, T s13,
+                                             const Cplx<T>* cached, int64_t i, int64_t n,
+                                             Cplx<T>* B, SwaveState<T>& w) {
+  constexpr int SP = sig_spins(SIG);
+  constexpr int NR = SP ? sig_count(SP) : kMaxRes;
+  if constexpr (CACHED) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < m.n_res) B[r] = cached[(int64_t)r * n + i];
+  } else if constexpr (std::is_same<T, float>::value) {
+    bw_basis<SP>(m, s12, s13, B);
+  } else {
+    bw_basis(m, s12, s13, B);
+  }
+  Cplx<T> A = combine<NR>(m, sm, B);
+  // the S-wave form: at run time, or fixed by a specialised kernel's signature
+  const bool reim = SIG == 0 ? m.reim != 0 : sig_reim(SIG);
+  swave_add(m, sm, s12, reim, w.c12, A);
+  swave_add(m, sm, s13, reim, w.c13, A);
+  return A;
+}
+
+template <typename T>
+__device__ __forceinline__ void bin_add(EvalSmem<T>& sm, int idx, T v) {
+  if constexpr (std::is_same<T, float>::value) {
+    atomicAdd(&sm.binf[idx], v);
+  } else {
+    atomicAdd(&sm.bind[idx], v);
+  }
+}
+
+// Adjoint of one channel's S-wave, as the 8 contributions to its segment's
+// polynomial bins: d|A|^2/d a(s) = 2 Re(A* e^{i phi}) and
+// d|A|^2/d phi(s) = 2 a Re(A* i e^{i phi}) (Re/Im form: d|A|^2/dx(s) = 2 Re A,
+// d|A|^2/dy(s) = 2 Im A), times t^m, t = s - s_j (the exact knot: the FP32
+// form evaluates about float(s_j) and shifts back here). Aw = 2 wt A: the
+// event's weight and the factor 2 applied once.
+template <typename T>
+__device__ __forceinline__ void swave_adjoint(const EvalSmem<T>& sm, const SwavePart<T>& w,
+                                              bool reim, Cplx<T> Aw, T* v) {
+  const T abar = reim ? Aw.re : Aw.re * w.cs + Aw.im * w.sn;
+  const T pbar = reim ? Aw.im : w.a * (Aw.im * w.cs - Aw.re * w.sn);
+  T t1 = w.t;
+  if constexpr (std::is_same<T, float>::value) t1 = w.t - sm.knot_lo[w.j];
+  const T t2 = t1 * t1, t3 = t2 * t1;
+  v[0] = abar;
+  v[1] = abar * t1;
+  v[2] = abar * t2;
+  v[3] = abar * t3;
+  v[4] = pbar;
+  v[5] = pbar * t1;
+  v[6] = pbar * t2;
+  v[7] = pbar * t3;
+}
+
+// Sum 16 values over the warp so that lanes 2i and 2i+1 both end with the
+// total of value i (recursive halving: 8 + 4 + 2 + 1 + 1 shuffles).
+template <typename T>
+__device__ __forceinline__ T reduce_scatter16(const T (&v)[16], int lane) {
+  constexpr unsigned full = 0xffffffffu;
+  T a8[8], a4[4], a2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    a8[k] = (h16 ? v[k + 8] : v[k]) + __shfl_xor_sync(full, h16 ? v[k] : v[k + 8], 16);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    a4[k] = (h8 ? a8[k + 4] : a8[k]) + __shfl_xor_sync(full, h8 ? a8[k] : a8[k + 4], 8);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    a2[k] = (h4 ? a4[k + 2] : a4[k]) + __shfl_xor_sync(full, h4 ? a4[k] : a4[k + 2], 4);
+  T a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(full, h2 ? a2[0] : a2[1], 2);
+  a1 += __shfl_xor_sync(full, a1, 1);
+  return a1;
+}
+
+// Bin the S-wave adjoint of the warp's events. Events come sorted by spline
+// cell, so the warp's live events nearly always share (j12, j13): then the
+// 16 contributions are summed over the warp first and 16 lanes add one total
+// each. Otherwise every lane adds its own 16 values.
+template <typename T>
+__device__ __forceinline__ void bin_swave_warp(EvalSmem<T>& sm, bool valid, int j12, int j13,
+                                               const T (&v)[16]) {
+  constexpr unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int key = valid ? (j12 << 6) | j13 : -1;
+  const unsigned have = __ballot_sync(full, valid);
+  if (!have) return;
+  const int k0 = __shfl_sync(full, key, __ffs(have) - 1);
+  if (__all_sync(full, !valid || key == k0)) {
+    const T tot = reduce_scatter16(v, lane);
+    if ((lane & 1) == 0) {
+      const int idx = lane >> 1;
+      const int j = idx < 8 ? (k0 >> 6) : (k0 & 63);
+      bin_add(sm, j * 8 + (idx & 7), tot);
+    }
+  } else if (valid) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) bin_add(sm, j12 * 8 + k, v[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) bin_add(sm, j13 * 8 + k, v[8 + k]);
+  }
+}
+
+// Add a thread's register sums of one cell (j12, j13) = (key >> 6, key & 63)
+// to the shared bins and clear them.
+template <typename T>
+__device__ __forceinline__ void flush_bins(EvalSmem<T>& sm, int key, T (&acc)[16]) {
+  const int j12 = key >> 6, j13 = key & 63;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    bin_add(sm, j12 * 8 + k, acc[k]);
+    bin_add(sm, j13 * 8 + k, acc[8 + k]);
+    acc[k] = T(0);
+    acc[8 + k] = T(0);
+  }
+}
+
+// The warp's register sums into the shared bins: one reduce-scatter when every
+// lane holding sums is in the same cell, else one lane at a time. All lanes of
+// the warp call this together; cur < 0 means "no sums".
+template <typename T>
+__device__ __forceinline__ void flush_bins_warp(EvalSmem<T>& sm, int cur, T (&acc)[16]) {
+  constexpr unsigned full = 0xffffffffu;
+  const unsigned have = __ballot_sync(full, cur >= 0);
+  if (!have) return;
+  const int k0 = __shfl_sync(full, cur, __ffs(have) - 1);
+  if (__all_sync(full, cur < 0 || cur == k0)) {
+    const int lane = threadIdx.x & 31;
+    const T tot = reduce_scatter16(acc, lane);
+    if ((lane & 1) == 0) {
+      const int idx = lane >> 1;
+      const int j = idx < 8 ? (k0 >> 6) : (k0 & 63);
+      bin_add(sm, j * 8 + (idx & 7), tot);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = T(0);
+  } else if (cur >= 0) {
+    flush_bins(sm, cur, acc);
+  }
+}
+
+// Reduce partial rows in a fixed order, then -2 ln L, its gradient and the
+// adjoint of the natural-spline solve (ybar += D^T T^{-1} Mbar). Data rows are
+// [d0, d0 + dn), normalisation rows [n0, n0 + nn); writes out[0..P] (BWG: and
+// the derivatives with respect to the resonance masses and widths at
+// out[1 + P .. 1 + P + 2R), from 2R extra columns at the end of each row).
+template <typename T, bool GRAD, bool BWG = false>
+__device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
+                              const double* partials, int d0, int dn, int n0, int nn,
+                              int64_t n_data, double norm_count, double* out, int* flags) {
+  const int R = m.n_res, N = m.kn.n, nseg = N - 1;
+  const int W0 = partial_width(N, R, GRAD);
+  const int W = W0 + (BWG ? 2 * R : 0);
+  for (int col = threadIdx.x; col < W; col += blockDim.x) {
+    double sd = 0.0, sn = 0.0;
+    for (int row = d0; row < d0 + dn; ++row) sd += __ldcg(&partials[(size_t)row * W + col]);
+    for (int row = n0; row < n0 + nn; ++row) sn += __ldcg(&partials[(size_t)row * W + col]);
+    sm.fin_d[col] = sd;
+    sm.fin_n[col] = sn;
+  }
+  __syncthreads();
+  const double S = sm.fin_n[0];
+  const double nd = (double)n_data;
+  if (threadIdx.x == 0) {
+    if (!(S > 0.0) || !isfinite(S)) atomicOr(flags, kFlagIntegral);
+    out[0] = -2.0 * sm.fin_d[0] + 2.0 * nd * log(S / norm_count);
+  }
+  if constexpr (GRAD) {
+    const double kappa = 2.0 * nd / S;
+    for (int col = 1 + threadIdx.x; col < W; col += blockDim.x)
+      sm.fin_d[col] = -2.0 * sm.fin_d[col] + kappa * sm.fin_n[col];
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * R; k += blockDim.x) {
+      // FP32 form: the kernel accumulated against A_r / cscale_r
+      const double sc = std::is_same<T, float>::value ? m.cscale[k >> 1] : 1.0;
+      out[1 + k] = sm.fin_d[1 + k] * sc;
+      if constexpr (BWG) out[1 + 2 * R + 2 * N + k] = sm.fin_d[W0 + k];
+    }
+    // one thread per spline, in different warps
+    const int sp = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 ? 1 : -1);
+    if (sp >= 0) {
+      const double* h = lu;
+      const double* ih = lu + nseg;
+      const double* w = lu + 2 * nseg;
+      const double* idia = w + (N - 2);
+      const double* sup = idia + (N - 2);
+      double* yb = sm.ybar[sp];
+      double* mb = sm.mbar[sp];
+      for (int k = 0; k < N; ++k) yb[k] = mb[k] = 0.0;
+      const double* G = &sm.fin_d[1 + 2 * R];
+      for (int j = 0; j < nseg; ++j) {
+        const double g0 = G[j * 8 + sp * 4 + 0], g1 = G[j * 8 + sp * 4 + 1];
+        const double g2 = G[j * 8 + sp * 4 + 2], g3 = G[j * 8 + sp * 4 + 3];
+        yb[j] += g0 - g1 * ih[j];
+        yb[j + 1] += g1 * ih[j];
+        mb[j] += -g1 * h[j] / 3.0 + 0.5 * g2 - g3 * ih[j] / 6.0;
+        mb[j + 1] += -g1 * h[j] / 6.0 + g3 * ih[j] / 6.0;
+      }
+      const int mm = N - 2;
+      if (mm >= 1) {
+        // v = T^{-1} Mbar_interior (T is symmetric), reusing mb[1..N-2] in place
+        double* v = mb + 1;
+        for (int i = 1; i < mm; ++i) v[i] -= w[i] * v[i - 1];
+        v[mm - 1] *= idia[mm - 1];
+        for (int i = mm - 2; i >= 0; --i) v[i] = (v[i] - sup[i] * v[i + 1]) * idia[i];
+        // (D y)_k = (y_{k+1} - y_k)/h_k - (y_k - y_{k-1})/h_{k-1}, k = 1..N-2
+        for (int k = 1; k <= N - 2; ++k) {
+          const double vk = v[k - 1];
+          yb[k + 1] += vk * ih[k];
+          yb[k] -= vk * (ih[k] + ih[k - 1]);
+          yb[k - 1] += vk * ih[k - 1];
+        }
+      }
+      for (int k = 0; k < N; ++k) out[1 + 2 * R + sp * N + k] = yb[k];
+    }
+  }
+}
+
+// Accumulate the events first, first + stride, ... < end of one sample
+// (cached basis: resonance-major over the sample's n events) into one partial
+// row: [sum ln|A|^2 (data) or sum |A|^2 (normalisation), c_r adjoint (2R),
+// spline polynomial adjoints (8 (N-1))]. The per-evaluation model data must be
+// staged in sm; the bins are zeroed here. Every thread of the block calls this.
+template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false,
+          bool WN = false>
+__device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
+                                 const Cplx<T>* cached, int64_t n, int64_t first, int64_t end,
+                                 int64_t stride, bool is_data, double* row, int* flags,
+                                 const double* coef64, const void* norm_w = nullptr) {
+  static_assert(!BWG || (std::is_same<T, double>::value && GRAD && !CACHED && SIG == 0),
+                "mass/width derivatives: FP64, direct, with the gradient");
+  const int R = m.n_res, nseg = m.kn.n - 1;
+  if constexpr (GRAD) {
+    for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) {
+      sm.bind[i] = 0.0;
+      sm.binf[i] = 0.0f;
+    }
+  }
+  __syncthreads();
+  Acc<T> sum;
+  T gc[2 * kMaxRes];  // c_r adjoint: plain sums (gradient tolerance), FP64 per block
+  double gb[BWG ? 2 * kMaxRes : 1];  // BWG: d/dm_r, d/dGamma_r of the sum
+#pragma unroll
+  for (int k = 0; k < 2 * kMaxRes; ++k) gc[k] = T(0);
+#pragma unroll
+  for (int k = 0; k < (BWG ? 2 * kMaxRes : 1); ++k) gb[k] = 0.0;
+  long long sum_e = 0;  // FP32 form, data: sum of binary exponents of |A|^2
+  int bad = 0;
+  int iter = 0;
+  // FP32 form: the spline adjoint of the thread's events is summed in
+  // registers while they stay in one spline cell (events are grouped by cell
+  // and a thread's consecutive events are 256 apart); every kRegIters
+  // iterations the warp adds its sums to the shared bins (one reduce-scatter
+  // when the warp shares the cell), and a lane whose cell changes adds its own.
+  // (Measured on the 40-knot workload: 64 iterations, once per flush of the
+  // shared bins to FP64, 0.8 % faster than 16.)
+  constexpr bool kThreadBins = std::is_same<T, float>::value;
+  constexpr int kRegIters = kFlushIters;
+  T acc[16];
+  int cur = -1;
+  int reg_iter = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = T(0);
+  // computed basis: the next iteration's event is loaded one iteration ahead
+  // (hides the global-load latency behind this iteration's arithmetic; with
+  // the cached basis the extra registers cost more than they hide)
+  EvT e_next{};
+  if constexpr (!CACHED) {
+    if (first + threadIdx.x < end) e_next = ev[first + threadIdx.x];
+  }
+  for (int64_t base = first; base < end; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    EvT e = e_next;
+    if constexpr (!CACHED) {
+      if (i + stride < end) e_next = ev[i + stride];
+    } else {
+      if (i < end) e = ev[i];
+    }
+    bool ok = false;
+    SwaveState<T> sw;
+    Cplx<T> A{T(0), T(0)};
+    Cplx<T> B[kMaxRes];
+    Cplx<double> dBm[BWG ? kMaxRes : 1], dBw[BWG ? kMaxRes : 1];
+    T wt = T(1);
+    if (i < end) {
+      const T s12 = (T)e.x, s13 = (T)e.y;
+      if constexpr (BWG) {
+        bw_basis_deriv(m, (double)s12, (double)s13, B, dBm, dBw);
+        A = combine<kMaxRes>(m, sm, B);
+        swave_add(m, sm, s12, m.reim != 0, sw.c12, A);
+        swave_add(m, sm, s13, m.reim != 0, sw.c13, A);
+      } else {
+        A = amplitude<T, SIG, CACHED>(m, sm, s12, s13, cached, i, n, B, sw);
+      }
+      const T A2 = A.re * A.re + A.im * A.im;
+      if (is_data) {
+        ok = A2 > T(0) && isfinite(A2);
+        if (ok) {
+          if constexpr (std::is_same<T, float>::value) {
+            int ex;
+            sum.add(log_split(A2, ex));
+            sum_e += ex;
+            wt = rcp_nr(A2);
+          } else {
+            sum.add(log(A2));
+            wt = A2 >= 2.2250738585072014e-308 ? rcp_d(A2) : T(1) / A2;
+          }
+        }
+      } else {
+        ok = isfinite(A2);
+        if (ok) {
+          if constexpr (WN) {  // weighted normalisation: w |A|^2, adjoint weight w
+            wt = (T)reinterpret_cast<const decltype(EvT::x)*>(norm_w)[i];
+            sum.add(wt * A2);
+          } else {
+            sum.add(A2);
+          }
+        }
+      }
+      bad |= ok ? 0 : 1;
+    }
+    if constexpr (GRAD) {
+      T v[16];
+      if (ok) {
+        const Cplx<T> Aw{T(2) * wt * A.re, T(2) * wt * A.im};  // d(wt |A|^2)/dA*
+        constexpr int NRg = sig_spins(SIG) ? sig_count(sig_spins(SIG)) : kMaxRes;
+#pragma unroll
+        for (int r = 0; r < NRg; ++r) {
+          if (sig_spins(SIG) || r < R) {
+            gc[2 * r] += Aw.re * B[r].re + Aw.im * B[r].im;
+            gc[2 * r + 1] += Aw.im * B[r].re - Aw.re * B[r].im;
+          }
+        }
+        if constexpr (BWG) {
+#pragma unroll
+          for (int r = 0; r < kMaxRes; ++r) {
+            if (r < R) {
+              // d|A|^2/dtheta = 2 Re(conj(A) c_r dB_r/dtheta)
+              const double cr = sm.cre[r], ci = sm.cim[r];
+              const double xm = cr * dBm[r].re - ci * dBm[r].im, ym = cr * dBm[r].im + ci * dBm[r].re;
+              const double xw = cr * dBw[r].re - ci * dBw[r].im, yw = cr * dBw[r].im + ci * dBw[r].re;
+              gb[2 * r] += Aw.re * xm + Aw.im * ym;
+              gb[2 * r + 1] += Aw.re * xw + Aw.im * yw;
+            }
+          }
+        }
+        const bool reim = SIG == 0 ? m.reim != 0 : sig_reim(SIG);
+        swave_adjoint(sm, sw.c12, reim, Aw, v);
+        swave_adjoint(sm, sw.c13, reim, Aw, v + 8);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = T(0);
+      }
+      if constexpr (kThreadBins) {
+        if (ok) {
+          const int key = (sw.j12() << 6) | sw.j13();
+          if (key != cur) {
+            if (cur >= 0) flush_bins(sm, cur, acc);
+            cur = key;
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k) acc[k] += v[k];
+        }
+        if (++reg_iter == kRegIters) {
+          reg_iter = 0;
+          flush_bins_warp(sm, cur, acc);
+        }
+      } else {
+        bin_swave_warp(sm, ok, ok ? sw.j12() : 0, ok ? sw.j13() : 0, v);
+      }
+    }
+    if constexpr (GRAD && std::is_same<T, float>::value) {
+      if (++iter == kFlushIters) {
+        iter = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < nseg * 8; k += blockDim.x) {
+          sm.bind[k] += (double)sm.binf[k];
+          sm.binf[k] = 0.0f;
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (bad) atomicOr(flags, is_data ? kFlagData : kFlagNorm);
+  if constexpr (GRAD && kThreadBins) flush_bins_warp(sm, cur, acc);
+  if constexpr (GRAD && std::is_same<T, float>::value) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < nseg * 8; k += blockDim.x) sm.bind[k] += (double)sm.binf[k];
+  }
+
+  // block reduction of the register sums (fixed order: shuffles, then warps)
+  const int nred = GRAD ? 1 + 2 * R + (BWG ? 2 * R : 0) : 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 1 + (BWG ? 4 : 2) * kMaxRes; ++k) {
+    if (k < nred) {
+      double v = 0.0;
+      if (k == 0) {
+        v = sum.value() + 0.69314718055994531 * (double)sum_e;
+      } else if (k <= 2 * R) {
+        v = (double)gc[k - 1];
+      } else {
+        if constexpr (BWG) v = gb[k - 1 - 2 * R];
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) sm.red[warp][k] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nred) {
+    double v = 0.0;
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) v += sm.red[wv][threadIdx.x];
+    const int k = threadIdx.x;
+    // BWG columns go after the polynomial adjoints
+    row[k <= 2 * R ? k : partial_width(m.kn.n, R, GRAD) + (k - 1 - 2 * R)] = v;
+  }
+  if constexpr (GRAD) {
+    for (int k = threadIdx.x; k < nseg * 8; k += blockDim.x) row[1 + 2 * R + k] = sm.bind[k];
+  }
+}
+
+// The model's compile-time signature, if a specialised FP32 kernel exists: a
+// P-wave and a D-wave, with either S-wave form.
+inline int model_sig(const Model& m) {
+  if (m.n_res == 2 && m.cf.L[0] == 1 && m.cf.L[1] == 2) return m.reim ? kSigPDReim : kSigPD;
+  return 0;
+}
+
+}  // namespace mipwa

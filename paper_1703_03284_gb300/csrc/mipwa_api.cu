@@ -7,6 +7,10 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/mipwa.h"
@@ -103,7 +107,13 @@ struct mipwa_ctx {
     double* h_out = nullptr;     // pinned (1+P per toy, then the flags)
     size_t h_cap = 0;            // doubles of each pinned buffer
     int n_items = 0, rows_per_toy = 0, norm_chunks = 0, grid = 0;
+    // launch configuration (mipwa_toys_config): work-item sizes, block size,
+    // resident blocks per SM of the persistent grid (0: as many as fit)
     int64_t norm_chunk = 131072, data_chunk = 65536;
+    int block = 256, blocks_per_sm = 0;
+    // autotuner: choices made on this context, and an optional file of them
+    std::vector<std::pair<std::string, mipwa_toys_config>> tuned;
+    std::string tune_file;
     bool planned = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -137,12 +147,16 @@ int fail(mipwa_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
+// A failed runtime call returns its status; the runtime's non-sticky "last
+// error" is cleared so that it does not surface in the caller's next check.
 #define CK(ctx, call)                                                                  \
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \
-    if (e_ != cudaSuccess)                                                             \
+    if (e_ != cudaSuccess) {                                                           \
+      cudaGetLastError();                                                              \
       return fail((ctx), e_ == cudaErrorMemoryAllocation ? MIPWA_ENOMEM : MIPWA_ECUDA, \
                   "%s: %s", #call, cudaGetErrorString(e_));                            \
+    }                                                                                  \
   } while (0)
 
 size_t ev_bytes(int dtype) { return dtype == MIPWA_F32 ? 2 * sizeof(float) : 2 * sizeof(double); }
@@ -227,11 +241,24 @@ void derive(Model& m, const mipwa_resonance* res, int n_res, double r_res, doubl
   }
 }
 
-// Eliminate the natural-spline tridiagonal system of the knots once (Thomas).
-void factor_spline(const Knots& kn, std::vector<double>& lu) {
+void set_knots(Knots& kn, const double* knots, int n_knots) {
+  kn.n = n_knots;
+  for (int k = 0; k < kMaxKnots; ++k) kn.s[k] = k < n_knots ? knots[k] : 0.0;
+  kn.s0 = knots[0];
+  kn.h = (knots[n_knots - 1] - knots[0]) / (n_knots - 1);
+  kn.inv_h = 1.0 / kn.h;
+  kn.s0_f = (float)kn.s0;
+  kn.inv_h_f = (float)kn.inv_h;
+  kn.uniform = 1;
+  const double scale = std::fabs(knots[0]) + std::fabs(knots[n_knots - 1]);
+  for (int k = 0; k < n_knots; ++k)
+    if (std::fabs(knots[k] - (kn.s0 + k * kn.h)) > 1e-12 * scale) kn.uniform = 0;
+}
+
+void factor_spline_into(const Knots& kn, double* lu) {
   const int N = kn.n, nseg = N - 1, mm = N - 2;
-  lu.assign(SplineLU::size(N), 0.0);
-  double* h = lu.data();
+  for (int i = 0; i < SplineLU::size(N); ++i) lu[i] = 0.0;
+  double* h = lu;
   double* ih = h + nseg;
   double* w = ih + nseg;
   double* idia = w + (mm > 0 ? mm : 0);
@@ -253,6 +280,21 @@ void factor_spline(const Knots& kn, std::vector<double>& lu) {
     idia[i] = 1.0 / dd;
     prev_dia = dd;
   }
+}
+
+void factor_spline(const Knots& kn, std::vector<double>& lu) {
+  lu.assign(SplineLU::size(kn.n), 0.0);
+  factor_spline_into(kn, lu.data());
+}
+
+int device_ptr_on(const void* p, int device) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (attr.type == cudaMemoryTypeManaged) return 1;
+  return attr.type == cudaMemoryTypeDevice && (device < 0 || attr.device == device);
 }
 
 }  // namespace mipwa
@@ -278,15 +320,13 @@ int check_ctx(mipwa_ctx* c) {
   return MIPWA_OK;
 }
 
-// Non-zero when p is device (or managed) memory the kernels may dereference.
-int is_device_ptr(const void* p) {
-  cudaPointerAttributes attr;
-  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
-}
+// Non-zero when p is memory the context's kernels may dereference: device
+// memory of the context's GPU, or managed memory.
+int is_device_ptr(const mipwa_ctx* c, const void* p) { return device_ptr_on(p, c->device); }
+
+// Non-zero when p is device memory of any GPU (or managed): a source that the
+// library only copies from (cudaMemcpyAsync reaches a peer GPU's memory).
+int is_copy_source(const void* p) { return device_ptr_on(p, -1); }
 
 int grid_for(mipwa_ctx* c, int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
@@ -382,7 +422,7 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
   const bool weighted = wptr != nullptr && n > 0;
   const size_t wbytes = (size_t)n * (dtype == MIPWA_F32 ? sizeof(float) : sizeof(double));
   if (weighted) {
-    if (on_device && !is_device_ptr(wptr))
+    if (on_device && !is_copy_source(wptr))
       return fail(c, MIPWA_EINVAL, "on_device set but the weights are not device memory");
     rc = ensure(c, &smp.w_spare, &smp.w_spare_cap, wbytes);
     if (rc) return rc;
@@ -396,7 +436,7 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
   *h_wsum = 0.0;
   if (n > 0) {
     if (on_device) {
-      if (!is_device_ptr(ptr))
+      if (!is_copy_source(ptr))
         return fail(c, MIPWA_EINVAL, "on_device set but the pointer is not device memory");
       CK(c, cudaMemcpyAsync(smp.spare, ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
     }
@@ -806,7 +846,7 @@ int enqueue_toys(mipwa_ctx* c, cudaStream_t st) {
   a.model = c->model;
   a.norm_w = (c->norm.weighted && !c->gram_on) ? c->norm.w_cur : nullptr;
   a.norm_count = c->norm.wsum;
-  CK(c, launch_toys(f32, ev32, a, q.grid, st));
+  CK(c, launch_toys(f32, ev32, a, q.block, q.grid, st));
   CK(c, cudaMemcpyAsync(q.h_out, q.d_out, (size_t)T * (1 + P) * sizeof(double),
                         cudaMemcpyDeviceToHost, st));
   CK(c, cudaMemcpyAsync(q.h_out + (size_t)T * (1 + P), c->d_flags, sizeof(int),
@@ -838,8 +878,13 @@ int run_toys(mipwa_ctx* c) {
     rc = plan_toys(c);
     if (rc) return rc;
   }
-  // persistent grid: every SM full (computed outside any stream capture)
-  q.grid = c->sm_count * toys_blocks_per_sm(c->mode == MIPWA_F32, c->norm.dtype == MIPWA_F32);
+  // persistent grid: blocks_per_sm (0: as many as fit) blocks on every SM
+  // (computed outside any stream capture)
+  const int occ = toys_blocks_per_sm(c->mode == MIPWA_F32, c->norm.dtype == MIPWA_F32,
+                                     c->basis_on, c->norm.weighted && !c->gram_on, c->model,
+                                     q.block);
+  if (occ < 1) return fail(c, MIPWA_EINVAL, "no batched kernel with %d threads per block", q.block);
+  q.grid = c->sm_count * (q.blocks_per_sm > 0 ? std::min(q.blocks_per_sm, occ) : occ);
   if (q.use_graph) {
     if (!q.exec) {
       CK(c, cudaStreamSynchronize(c->stream));
@@ -863,6 +908,143 @@ int run_toys(mipwa_ctx* c) {
     c->launches += c->gram_on ? 4 : 3;
   }
   CK(c, cudaStreamSynchronize(c->stream));
+  return MIPWA_OK;
+}
+
+// Key of the autotuner's choice: what decides the work list and the kernel
+// (model signature, forms, compute mode, event dtype, sample sizes, SMs).
+std::string tune_key(const mipwa_ctx* c) {
+  std::ostringstream k;
+  const Model& m = c->model;
+  k << "m" << c->mode << "_e" << c->norm.dtype << "_R" << m.n_res << "_L";
+  for (int r = 0; r < m.n_res; ++r) k << m.cd.L[r];
+  k << "_N" << m.kn.n << "_u" << m.kn.uniform << "_f" << m.reim << "_b" << (c->basis_on ? 1 : 0)
+    << "_g" << (c->gram_on ? 1 : 0) << "_w" << (c->norm.weighted ? 1 : 0) << "_nn" << c->norm.n
+    << "_T" << c->tq.n << "_nt" << c->toys.n << "_sm" << c->sm_count;
+  return k.str();
+}
+
+// The last line of the file with this key, if any: "key norm data block bps".
+bool read_tune_file(const std::string& path, const std::string& key, mipwa_toys_config* cfg) {
+  std::ifstream f(path);
+  if (!f) return false;
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream in(line);
+    std::string k;
+    mipwa_toys_config v{};
+    if (!(in >> k >> v.norm_chunk >> v.data_chunk >> v.block >> v.blocks_per_sm)) continue;
+    if (k != key) continue;
+    const bool ok = v.norm_chunk >= kThreads && v.norm_chunk <= ((int64_t)1 << 30) &&
+                    v.data_chunk >= kThreads && v.data_chunk <= ((int64_t)1 << 30) &&
+                    (v.block == 128 || v.block == 256 || v.block == 512) &&
+                    v.blocks_per_sm >= 0 && v.blocks_per_sm <= 16;
+    if (ok) {
+      *cfg = v;
+      found = true;
+    }
+  }
+  return found;
+}
+
+// Milliseconds of one batched evaluation at the context's configuration (the
+// best of two after a warm-up that plans and captures).
+int time_toys(mipwa_ctx* c, float* ms) {
+  int rc = run_toys(c);
+  if (rc) return rc;
+  *ms = 0.0f;
+  for (int rep = 0; rep < 2; ++rep) {
+    CK(c, cudaEventRecord(c->ev0, c->stream));
+    rc = run_toys(c);
+    if (rc) return rc;
+    CK(c, cudaEventRecord(c->ev1, c->stream));
+    CK(c, cudaEventSynchronize(c->ev1));
+    float t = 0.0f;
+    CK(c, cudaEventElapsedTime(&t, c->ev0, c->ev1));
+    if (rep == 0 || t < *ms) *ms = t;
+  }
+  return MIPWA_OK;
+}
+
+// Coordinate search over the launch configuration: normalisation chunk, data
+// chunk, block size, blocks per SM, then the normalisation chunk once more.
+// Candidates that give the same work list as a smaller one are skipped.
+int tune_toys(mipwa_ctx* c, mipwa_toys_config* out, int* n_timed) {
+  auto& q = c->tq;
+  mipwa_toys_config cur{q.norm_chunk, q.data_chunk, q.block, q.blocks_per_sm};
+  float best_ms = -1.0f;
+  int timed = 0;
+  auto try_cfg = [&](const mipwa_toys_config& v) -> int {
+    int rc = mipwa_set_toys_config(c, &v);
+    if (rc) return rc;
+    float ms = 0.0f;
+    rc = time_toys(c, &ms);
+    if (rc) return rc;
+    ++timed;
+    if (best_ms < 0.0f || ms < best_ms) {
+      best_ms = ms;
+      cur = v;
+    }
+    return MIPWA_OK;
+  };
+  int rc = try_cfg(cur);
+  if (rc) return rc;
+  const int64_t nn = c->norm.n;
+  int64_t max_toy = 0;
+  for (int t = 0; t < q.n; ++t) max_toy = std::max(max_toy, q.offsets[t + 1] - q.offsets[t]);
+  auto norm_pass = [&]() -> int {
+    if (c->gram_on) return MIPWA_OK;  // no normalisation items
+    int64_t prev_count = -1;
+    for (int64_t ch : {65536, 131072, 262144, 524288, 1048576, 2097152}) {
+      const int64_t count = (nn + ch - 1) / ch;
+      if (count == prev_count) continue;
+      prev_count = count;
+      if (ch == cur.norm_chunk) continue;
+      mipwa_toys_config v = cur;
+      v.norm_chunk = ch;
+      const int rc2 = try_cfg(v);
+      if (rc2) return rc2;
+    }
+    return MIPWA_OK;
+  };
+  rc = norm_pass();
+  if (rc) return rc;
+  int64_t prev_rows = -1;
+  for (int64_t ch : {32768, 65536, 131072, 262144}) {
+    const int64_t rows = (max_toy + ch - 1) / ch;
+    if (rows == prev_rows) continue;
+    prev_rows = rows;
+    if (ch == cur.data_chunk) continue;
+    mipwa_toys_config v = cur;
+    v.data_chunk = ch;
+    rc = try_cfg(v);
+    if (rc) return rc;
+  }
+  const bool weighted = c->norm.weighted && !c->gram_on;
+  for (int bs : {128, 256, 512}) {
+    if (bs == cur.block) continue;
+    if (toys_blocks_per_sm(c->mode == MIPWA_F32, c->norm.dtype == MIPWA_F32, c->basis_on,
+                           weighted, c->model, bs) < 1)
+      continue;
+    mipwa_toys_config v = cur;
+    v.block = bs;
+    v.blocks_per_sm = 0;
+    rc = try_cfg(v);
+    if (rc) return rc;
+  }
+  const int occ = toys_blocks_per_sm(c->mode == MIPWA_F32, c->norm.dtype == MIPWA_F32,
+                                     c->basis_on, weighted, c->model, cur.block);
+  for (int b = 1; b < occ; ++b) {
+    mipwa_toys_config v = cur;
+    v.blocks_per_sm = b;
+    rc = try_cfg(v);
+    if (rc) return rc;
+  }
+  rc = norm_pass();
+  if (rc) return rc;
+  *out = cur;
+  if (n_timed) *n_timed = timed;
   return MIPWA_OK;
 }
 
@@ -1022,20 +1204,9 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   }
   Model m = c->model;
   derive(m, res, n_res, r_res, r_D);
-  Knots& kn = m.kn;
-  kn.n = n_knots;
-  for (int k = 0; k < kMaxKnots; ++k) kn.s[k] = k < n_knots ? knots[k] : 0.0;
-  kn.s0 = knots[0];
-  kn.h = (knots[n_knots - 1] - knots[0]) / (n_knots - 1);
-  kn.inv_h = 1.0 / kn.h;
-  kn.s0_f = (float)kn.s0;
-  kn.inv_h_f = (float)kn.inv_h;
-  kn.uniform = 1;
-  const double scale = std::fabs(knots[0]) + std::fabs(knots[n_knots - 1]);
-  for (int k = 0; k < n_knots; ++k)
-    if (std::fabs(knots[k] - (kn.s0 + k * kn.h)) > 1e-12 * scale) kn.uniform = 0;
+  set_knots(m.kn, knots, n_knots);
   std::vector<double> lu;
-  factor_spline(kn, lu);
+  factor_spline(m.kn, lu);
   CK(c, cudaMemcpyAsync(c->d_lu, lu.data(), lu.size() * sizeof(double), cudaMemcpyHostToDevice,
                         c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
@@ -1212,38 +1383,88 @@ int mipwa_nll_grad_toys(mipwa_ctx* c, const double* params, double* nll, double*
   return MIPWA_OK;
 }
 
-int mipwa_toys_autotune(mipwa_ctx* c, const double* params, int64_t* best_chunk) {
+int mipwa_set_toys_config(mipwa_ctx* c, const mipwa_toys_config* cfg) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!cfg) return fail(c, MIPWA_EINVAL, "null pointer");
+  const int64_t lo = kThreads, hi = (int64_t)1 << 30;
+  if ((cfg->norm_chunk && (cfg->norm_chunk < lo || cfg->norm_chunk > hi)) ||
+      (cfg->data_chunk && (cfg->data_chunk < lo || cfg->data_chunk > hi)))
+    return fail(c, MIPWA_EINVAL, "chunks must be 0 or in %lld..%lld events", (long long)lo,
+                (long long)hi);
+  if (cfg->block && cfg->block != 128 && cfg->block != 256 && cfg->block != 512)
+    return fail(c, MIPWA_EINVAL, "block must be 0, 128, 256 or 512");
+  if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 16)
+    return fail(c, MIPWA_EINVAL, "blocks_per_sm must be in 0..16");
+  auto& q = c->tq;
+  if (cfg->norm_chunk) q.norm_chunk = cfg->norm_chunk;
+  if (cfg->data_chunk) q.data_chunk = cfg->data_chunk;
+  if (cfg->block) q.block = cfg->block;
+  q.blocks_per_sm = cfg->blocks_per_sm;
+  q.planned = false;
+  invalidate_graph(c);
+  return MIPWA_OK;
+}
+
+int mipwa_get_toys_config(mipwa_ctx* c, mipwa_toys_config* cfg) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!cfg) return fail(c, MIPWA_EINVAL, "null pointer");
+  cfg->norm_chunk = c->tq.norm_chunk;
+  cfg->data_chunk = c->tq.data_chunk;
+  cfg->block = c->tq.block;
+  cfg->blocks_per_sm = c->tq.blocks_per_sm;
+  return MIPWA_OK;
+}
+
+int mipwa_set_toys_tune_file(mipwa_ctx* c, const char* path) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->tq.tune_file = path ? path : "";
+  return MIPWA_OK;
+}
+
+int mipwa_toys_autotune(mipwa_ctx* c, const double* params, mipwa_toys_config* best,
+                        int* n_timed) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!params) return fail(c, MIPWA_EINVAL, "null pointer");
   auto& q = c->tq;
   const int T = q.n, P = c->n_params;
   if (T == 0 || !c->have_model) return fail(c, MIPWA_ESTATE, "set_toys and set_model first");
-  std::memcpy(q.h_params, params, (size_t)T * P * sizeof(double));
-  const int64_t cand[] = {65536, 131072, 262144, 524288, 1048576, 2097152};
-  float best_ms = 0.0f;
-  int64_t best = q.norm_chunk;
-  cudaEvent_t e0 = c->ev0, e1 = c->ev1;
-  for (int64_t ch : cand) {
-    q.norm_chunk = ch;
-    q.planned = false;
-    rc = run_toys(c);  // plan, capture and warm up
-    if (rc) return rc;
-    CK(c, cudaEventRecord(e0, c->stream));
-    rc = run_toys(c);
-    if (rc) return rc;
-    CK(c, cudaEventRecord(e1, c->stream));
-    CK(c, cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    CK(c, cudaEventElapsedTime(&ms, e0, e1));
-    if (best_ms == 0.0f || ms < best_ms) {
-      best_ms = ms;
-      best = ch;
+  for (size_t k = 0; k < (size_t)T * P; ++k)
+    if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %zu is not finite", k);
+  if (n_timed) *n_timed = 0;
+  const std::string key = tune_key(c);
+  mipwa_toys_config cfg{};
+  bool found = false;
+  for (const auto& kv : q.tuned)
+    if (kv.first == key) {
+      cfg = kv.second;
+      found = true;
     }
+  if (!found && !q.tune_file.empty()) found = read_tune_file(q.tune_file, key, &cfg);
+  if (found) {
+    rc = mipwa_set_toys_config(c, &cfg);
+    if (rc) return rc;
+    if (std::none_of(q.tuned.begin(), q.tuned.end(),
+                     [&](const auto& kv) { return kv.first == key; }))
+      q.tuned.emplace_back(key, cfg);
+    if (best) *best = cfg;
+    return MIPWA_OK;
   }
-  q.norm_chunk = best;
-  q.planned = false;
-  if (best_chunk) *best_chunk = best;
+  std::memcpy(q.h_params, params, (size_t)T * P * sizeof(double));
+  rc = tune_toys(c, &cfg, n_timed);
+  if (rc) return rc;
+  rc = mipwa_set_toys_config(c, &cfg);
+  if (rc) return rc;
+  q.tuned.emplace_back(key, cfg);
+  if (!q.tune_file.empty()) {
+    std::ofstream f(q.tune_file, std::ios::app);
+    if (f) f << key << ' ' << cfg.norm_chunk << ' ' << cfg.data_chunk << ' ' << cfg.block << ' '
+             << cfg.blocks_per_sm << '\n';
+  }
+  if (best) *best = cfg;
   return MIPWA_OK;
 }
 
@@ -1262,7 +1483,7 @@ int mipwa_amp2(mipwa_ctx* c, const double* params, const void* ev, int64_t n, in
   if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
   if (!params || n < 0 || (n > 0 && (!ev || !out))) return fail(c, MIPWA_EINVAL, "bad argument");
   if (dtype != MIPWA_F32 && dtype != MIPWA_F64) return fail(c, MIPWA_EINVAL, "bad dtype");
-  if (n > 0 && (!is_device_ptr(ev) || !is_device_ptr(out)))
+  if (n > 0 && (!is_device_ptr(c, ev) || !is_device_ptr(c, out)))
     return fail(c, MIPWA_EINVAL, "amp2 takes device pointers");
   for (int k = 0; k < c->n_params; ++k)
     if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
@@ -1286,7 +1507,7 @@ int mipwa_inside(mipwa_ctx* c, const void* ev, int64_t n, int dtype, uint8_t* ou
   if (n < 0 || (n > 0 && (!ev || !out))) return fail(c, MIPWA_EINVAL, "bad argument");
   if (dtype != MIPWA_F32 && dtype != MIPWA_F64) return fail(c, MIPWA_EINVAL, "bad dtype");
   if (n == 0) return MIPWA_OK;
-  if (!is_device_ptr(ev) || !is_device_ptr(out))
+  if (!is_device_ptr(c, ev) || !is_device_ptr(c, out))
     return fail(c, MIPWA_EINVAL, "inside takes device pointers");
   CK(c, launch_inside(dtype == MIPWA_F32, c->model, ev, n, out, nullptr, grid_for(c, n),
                       c->stream));
@@ -1307,7 +1528,7 @@ int mipwa_get_sample(mipwa_ctx* c, int which, void* out, int64_t n_cap, int64_t*
   if (!out || smp.n == 0) return MIPWA_OK;
   if (n_cap < smp.n) return fail(c, MIPWA_EINVAL, "n_cap %lld < %lld events", (long long)n_cap,
                                  (long long)smp.n);
-  if (!is_device_ptr(out)) return fail(c, MIPWA_EINVAL, "get_sample takes a device pointer");
+  if (!is_copy_source(out)) return fail(c, MIPWA_EINVAL, "get_sample takes a device pointer");
   CK(c, cudaMemcpyAsync(out, smp.cur, (size_t)smp.n * ev_bytes(smp.dtype),
                         cudaMemcpyDeviceToDevice, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));

@@ -10,6 +10,7 @@
 namespace mipwa {
 
 constexpr int kThreads = 256;        // threads per block of the event kernels
+constexpr int kMaxBlock = 512;       // largest block of the batched-toys kernel
 constexpr int kFlushIters = 64;      // FP32 form: grid-stride iterations between bin flushes
 
 struct EvalArgs {
@@ -73,9 +74,15 @@ struct ToyArgs {
 // coef + s*coef_size and coef32 + s*coef32_size.
 void launch_prepare(const Model& m, const double* params, const double* lu, double* coef,
                     float* coef32, cudaStream_t stream, int n_sets = 1);
-cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int grid,
+// The batched-toys kernel (block = 128, 256 or 512 threads; weighted
+// normalisation: 256 only) and the per-toy reduction. cudaErrorInvalidValue
+// for a block size without a kernel.
+cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int block, int grid,
                         cudaStream_t stream);
-int toys_blocks_per_sm(int compute_f32, int ev_f32);
+// Resident blocks per SM of the batched-toys kernel that runs for these
+// arguments at this block size (0: no such kernel).
+int toys_blocks_per_sm(int compute_f32, int ev_f32, bool cached, bool weighted, const Model& m,
+                       int block);
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t stream);
 // FP64 NLL + gradient + d/d(m_r, Gamma_r) (no cached basis, direct

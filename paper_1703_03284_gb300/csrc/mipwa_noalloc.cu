@@ -64,46 +64,11 @@ cudaError_t scratch_address(int device, double** out) {
   return cudaSuccess;
 }
 
-void factor_into(const Knots& kn, double* lu) {
-  const int N = kn.n, nseg = N - 1, mm = N - 2;
-  double* h = lu;
-  double* ih = h + nseg;
-  double* w = ih + nseg;
-  double* idia = w + (mm > 0 ? mm : 0);
-  double* sup = idia + (mm > 0 ? mm : 0);
-  for (int j = 0; j < nseg; ++j) {
-    h[j] = kn.s[j + 1] - kn.s[j];
-    ih[j] = 1.0 / h[j];
-  }
-  double prev = 0.0;
-  for (int i = 0; i < mm; ++i) {
-    const int k = i + 1;
-    const double sub = h[k - 1] / 6.0, dia = (h[k - 1] + h[k]) / 3.0;
-    sup[i] = h[k] / 6.0;
-    w[i] = 0.0;
-    double dd = dia;
-    if (i > 0) {
-      w[i] = sub / prev;
-      dd = dia - w[i] * sup[i - 1];
-    }
-    idia[i] = 1.0 / dd;
-    prev = dd;
-  }
-}
-
-int is_device_ptr(const void* p) {
-  cudaPointerAttributes attr;
-  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
-}
-
 #define CKN(call)                                                                  \
   do {                                                                             \
     const cudaError_t e_ = (call);                                                 \
     if (e_ != cudaSuccess) {                                                       \
+      cudaGetLastError(); /* clear the non-sticky last error */                    \
       std::fprintf(stderr, "mipwa_nll_grad_noalloc: %s: %s\n", #call,              \
                    cudaGetErrorString(e_));                                        \
       return MIPWA_ECUDA;                                                          \
@@ -142,7 +107,10 @@ extern "C" int mipwa_nll_grad_noalloc(int device, int compute_mode, double mD, d
     if (!std::isfinite(params[k])) return MIPWA_EINVAL;
 
   CKN(cudaSetDevice(device));
-  if ((n_data > 0 && !is_device_ptr(d_data)) || !is_device_ptr(d_norm) || !is_device_ptr(d_out))
+  // the kernels read the events and write the result directly: all three
+  // buffers must be memory of `device` (or managed)
+  if ((n_data > 0 && !device_ptr_on(d_data, device)) || !device_ptr_on(d_norm, device) ||
+      !device_ptr_on(d_out, device))
     return MIPWA_EINVAL;
   double* scratch = nullptr;
   CKN(scratch_address(device, &scratch));
@@ -154,28 +122,16 @@ extern "C" int mipwa_nll_grad_noalloc(int device, int compute_mode, double mD, d
   m.m1 = m1;
   m.m2 = m2;
   derive(m, res, n_res, r_res, r_D);
-  Knots& kn = m.kn;
-  kn.n = n_knots;
-  for (int k = 0; k < kMaxKnots; ++k) kn.s[k] = k < n_knots ? knots[k] : 0.0;
-  kn.s0 = knots[0];
-  kn.h = (knots[n_knots - 1] - knots[0]) / (n_knots - 1);
-  kn.inv_h = 1.0 / kn.h;
-  kn.s0_f = (float)kn.s0;
-  kn.inv_h_f = (float)kn.inv_h;
-  kn.uniform = 1;
-  const double scale = std::fabs(knots[0]) + std::fabs(knots[n_knots - 1]);
-  for (int k = 0; k < n_knots; ++k)
-    if (std::fabs(knots[k] - (kn.s0 + k * kn.h)) > 1e-12 * scale) kn.uniform = 0;
+  set_knots(m.kn, knots, n_knots);
   double lu[kLU];
-  factor_into(kn, lu);
+  factor_spline_into(m.kn, lu);
 
-  // ---- grid: as the context API, capped at the scratch rows
-  int sm_count = 0, per_sm0 = 0, per_sm1 = 0;
+  // ---- grid: as the context API (SMs x resident blocks), capped at the
+  // scratch rows (608 = 152 SMs x 4 blocks: the whole grid on GB300)
+  int sm_count = 0;
   CKN(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
   const int f32 = compute_mode == MIPWA_F32, ev32 = dtype == MIPWA_F32;
-  per_sm0 = eval_blocks_per_sm(f32, ev32, m, false);
-  per_sm1 = per_sm0;
-  int total = sm_count * (per_sm0 < per_sm1 ? per_sm0 : per_sm1);
+  int total = sm_count * eval_blocks_per_sm(f32, ev32, m, false);
   if (total > kRows) total = kRows;
   if (total < 2) total = 2;
   const int64_t need_d = (n_data + kThreads - 1) / kThreads;
@@ -234,9 +190,13 @@ extern "C" int mipwa_nll_grad_noalloc(int device, int compute_mode, double mD, d
   a.basis_norm = nullptr;
   a.model = m;
   CKN(launch_eval(f32, ev32, true, a, nb_d + nb_n, st));
+  // the flags and the NLL come back together: a bad event, a non-positive
+  // integral or a non-finite -2 ln L is MIPWA_ENONPOS, as in mipwa_nll_grad
   int h_flags = 0;
+  double h_nll = 0.0;
   CKN(cudaMemcpyAsync(&h_flags, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKN(cudaMemcpyAsync(&h_nll, d_out, sizeof(double), cudaMemcpyDeviceToHost, st));
   CKN(cudaStreamSynchronize(st));
-  if (h_flags) return MIPWA_ENONPOS;
+  if (h_flags || !std::isfinite(h_nll)) return MIPWA_ENONPOS;
   return MIPWA_OK;
 }

@@ -49,6 +49,20 @@ def test_constants_match_header():
     for name in ("OK", "EINVAL", "EOUTSIDE", "ENONPOS", "ECUDA", "ETIMEOUT", "ESTATE", "ENOMEM"):
         m = re.search(rf"MIPWA_{name} = (-?\d+)", src)
         assert int(m.group(1)) == getattr(_lib, name)
+    for name in ("FFMA", "FFMA2", "DFMA", "MUFU"):
+        m = re.search(rf"#define MIPWA_PROBE_{name} (\d+)", src)
+        assert int(m.group(1)) == getattr(_lib, f"PROBE_{name}")
+
+
+def test_toys_config_layout_matches_header():
+    """mipwa_toys_config: two int64 chunks, then two ints (24 bytes)."""
+    from paper_1703_03284_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "mipwa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\} mipwa_toys_config;", src).group(1)
+    fields = re.findall(r"(int64_t|int)\s+(\w+);", body)
+    assert [n for _, n in fields] == [n for n, _ in _lib.ToysConfig._fields_]
+    assert ctypes.sizeof(_lib.ToysConfig) == 24
 
 
 def test_null_context_is_rejected(lib):

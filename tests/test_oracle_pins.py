@@ -710,3 +710,89 @@ def test_reim_gradient_central_differences(spec):
         e[k] = h
         fd[k] = (o.nll(p + e, data, norm) - o.nll(p - e, data, norm)) / (2 * h)
     np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-5 * np.abs(g).max())
+
+
+# ------------------------------------------------ gradient in the local form
+@pytest.mark.parametrize("spec", [synth.pipipi(10), synth.kpipi(12), synth.as_reim(synth.pipipi(10)),
+                                  synth.kkk(40)], ids=lambda s: s.name)
+def test_local_form_gradient_equals_dense(spec):
+    """The adjoint summed in segment bins and mapped to the knots once (the
+    local form the flop count follows) equals the dense per-event form."""
+    o = oracle.Oracle(spec)
+    truth = synth.true_params(spec)
+    data = synth.accept_reject(spec, 3000, synth.numpy_density(lambda x: o.density(truth, x)),
+                               seed=3).numpy()
+    norm = synth.uniform_in_plot(spec, 4000, synth.numpy_density(
+        lambda x: o.inside(x).astype(np.float64)), seed=4).numpy()
+    p = synth.perturbed_params(spec, 8)
+    w = 0.5 + np.random.default_rng(2).random(len(norm))
+    for wts in (None, w):
+        v, g = o.nll_grad(p, data, norm, norm_weights=wts)
+        vl, gl = o.nll_grad_local(p, data, norm, norm_weights=wts)
+        assert vl == pytest.approx(v, rel=1e-13)
+        assert np.linalg.norm(gl - g) <= 1e-11 * np.linalg.norm(g)
+
+
+# ------------------------------------------------------------- flop counting
+def test_flop_counter_closed_form():
+    """No resonances, two knots, Re/Im S-wave (a linear spline, M = 0): per
+    channel A_ = s1 - s and B_ = s - s0 (2), x(s) = c0 A_ + c1 B_ (3), y(s) (3 more,
+    A_ and B_ shared): 8; both channels and their sum 18; |A|^2 3; the running sum
+    1; ln 1 (data). Gradient: w = 1/|A|^2 and 2w (data), Abar (2); per channel
+    the four basis functions A_/h, B_/h, (A_^3/h - h A_)/6 and the same in B_
+    (2 + 12) and 8 products and 8 bin sums: 30 per channel."""
+    spec = synth.ModelSpec(name="count", mD=synth.M_D, m1=synth.M_PI, m2=synth.M_PI,
+                           resonances=(), knots=(0.078, 2.987), swave_form="reim")
+    o = oracle.Oracle(spec)
+    p = np.array([1.0, 0.5, 0.3, -0.2])
+    ev = np.array([[0.5, 1.2], [1.0, 0.9], [2.0, 0.4]])
+    assert o.count_flops(p, ev, True, False)["total"] == 23
+    assert o.count_flops(p, ev, False, False)["total"] == 22
+    assert o.count_flops(p, ev, True, True)["total"] == 23 + 4 + 60
+    assert o.count_flops(p, ev, False, True)["total"] == 22 + 2 + 60
+    c = o.count_flops(p, ev, True, False)
+    assert (c["add"], c["mul"], c["div"], c["sqrt"], c["func"]) == (12, 10, 0, 0, 1)
+
+
+def test_flop_counter_cse_and_cached_basis():
+    """Repeating the Breit-Wigner terms inside the gradient costs nothing (the
+    same operations on the same operands), and a stored basis removes exactly
+    the Breit-Wigner work: the cached count equals the direct count minus the
+    symmetrised basis's own operations."""
+    spec = synth.pipipi(10)
+    o = oracle.Oracle(spec)
+    p = synth.perturbed_params(spec, 3)
+    ev = synth.uniform_in_plot(spec, 200, synth.numpy_density(
+        lambda x: o.inside(x).astype(np.float64)), seed=9).numpy()
+    d = o.count_flops(p, ev, False, False, cached=False)["total"]
+    c = o.count_flops(p, ev, False, False, cached=True)["total"]
+    dg = o.count_flops(p, ev, False, True, cached=False)["total"]
+    cg = o.count_flops(p, ev, False, True, cached=True)["total"]
+    assert d - c == pytest.approx(dg - cg, abs=1e-9)
+    assert d - c > 100
+
+
+def test_bench_flop_constants_are_the_oracle_counts():
+    """The algorithmic flops per event that bench.py divides by are the
+    oracle's counts on the benchmark's model and parameters, averaged over
+    PDF-drawn data and uniform normalisation events in equal numbers."""
+    import bench
+    spec = synth.pipipi(40)
+    o = oracle.Oracle(spec)
+    truth = synth.true_params(spec)
+    p = synth.perturbed_params(spec, 3)
+    data = synth.accept_reject(spec, 20000, synth.numpy_density(lambda x: o.density(truth, x)),
+                               seed=7).numpy()
+    norm = synth.uniform_in_plot(spec, 20000, synth.numpy_density(
+        lambda x: o.inside(x).astype(np.float64)), seed=8).numpy()
+
+    def mean(grad, cached, sp=spec):
+        oo = oracle.Oracle(sp)
+        return 0.5 * (oo.count_flops(p, data, True, grad, cached)["total"] +
+                      oo.count_flops(p, norm, False, grad, cached)["total"])
+    assert bench.FLOPS_PER_EVENT_FWD == pytest.approx(mean(False, False), abs=0.5)
+    assert bench.FLOPS_PER_EVENT_GRAD == pytest.approx(mean(True, False), abs=0.5)
+    assert bench.FLOPS_PER_EVENT_GRAD_CACHED == pytest.approx(mean(True, True), abs=0.5)
+    reim = synth.as_reim(spec)
+    assert bench.FLOPS_PER_EVENT_GRAD_REIM == pytest.approx(mean(True, False, reim), abs=0.5)
+    assert bench.FLOPS_PER_EVENT_GRAD_REIM_CACHED == pytest.approx(mean(True, True, reim), abs=0.5)
