@@ -94,20 +94,22 @@ def parse():
     ap.add_argument("--n-toys", type=int, default=256)
     ap.add_argument("--toys-norm", type=int, default=10_000_000)
     ap.add_argument("--paper-fit", type=int, default=1,
-                    help="run the Sec. 4 workload (K K K, 40 knots, 100K toy) as full fits")
+                    help="run the Sec. 4 workload (K K K, 40 knots, 100K toys) as full fits")
+    ap.add_argument("--paper-toys", type=int, default=20,
+                    help="toys fitted at each normalisation grid spacing (Fig. 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi every 50 ms in a child process; a reader thread stamps each
+    """nvidia-smi every 25 ms in a child process; a reader thread stamps each
     sample on arrival, and stop() keeps the samples that arrived between
     begin() and end() (plus one sampling period), i.e. during the timed loop."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-    PERIOD_S = 0.05
+    PERIOD_S = 0.025
 
     def __init__(self, gpu: int):
         self.gpu = gpu
@@ -538,13 +540,17 @@ PAPER_FIT_SECONDS = {"Tesla K40c": 76, "GeForce GTX 980": 67, "GeForce GT 650M":
                      "2x Xeon E5-2680 v3, 24 threads": 50, "same, 1 thread": 791}
 
 
-def paper_fit_leg(rank):
+def paper_fit_leg(rank, n_toys: int = 20):
     """The workload of Sec. 4: D+ -> K- K+ K+ with the phi(1020) P-wave and a
-    40-knot K+K- S-wave, one 100K-event toy drawn from the model, fitted with
-    the normalisation on evenly spaced grids of 0.01, 0.004 and 0.001 GeV^2
-    (Fig. 2). Reports the wall time of each full fit (BFGS + Newton steps +
-    Hessian errors, FP64, as the paper's Table 1 reports fit times) and the
-    per-knot pulls (fit - input)/sigma of the magnitudes and phases."""
+    40-knot K+K- S-wave, toys of 100K events drawn from the model, each fitted
+    with the normalisation on evenly spaced grids of 0.01, 0.004 and 0.001
+    GeV^2 (Fig. 2: fitted minus input values at each boundary point for the
+    three spacings). Reports per spacing the wall time of the full fits (BFGS
+    + Newton steps + Hessian errors, FP64, as the paper's Table 1 reports fit
+    times) and, over the toys, the mean and spread of (fit - input) and of the
+    pulls (fit - input)/sigma at every knot, for the magnitudes a_k and the
+    phases phi_k; the overall mean pull with its error, and the chi^2 of the
+    per-knot mean pulls against zero."""
     import numpy as np
     import scipy.optimize  # noqa: F401  (imported here, outside the timed fits)
     import torch
@@ -555,33 +561,58 @@ def paper_fit_leg(rank):
 
     spec = synth.kkk(40)
     truth = synth.true_params(spec)
+    R, N = spec.n_res, spec.n_knots
     dev = torch.cuda.current_device()
     lik = Likelihood(dev, F64)
     lik.set_spec(spec)
-    data = synth.accept_reject(spec, 100_000, lambda x: lik.amp2(truth, x), seed=42 + rank,
-                               device="cuda")
-    lik.set_events(data)
-    start = synth.perturbed_params(spec, 43, 0.02)
-    start[:2] = truth[:2]
+    toys = [synth.accept_reject(spec, 100_000, lambda x: lik.amp2(truth, x),
+                                seed=42 + 1000 * rank + t, device="cuda") for t in range(n_toys)]
+    starts = []
+    for t in range(n_toys):
+        st = synth.perturbed_params(spec, 43 + t, 0.02)
+        st[:2 * R] = truth[:2 * R]
+        starts.append(st)
+    knots = slice(2 * R, 2 * R + 2 * N)
     out = []
     for spacing in (0.01, 0.004, 0.001):
         grid = synth.spacing_grid_in_plot(spec, spacing, lambda x: lik.inside(x).to(torch.float64),
                                           device="cuda")
         lik.set_norm_sample(grid)
-        for _ in range(3):
-            lik.nll_grad(start)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = fit(lik, start, fixed=(0, 1))
-        dt = time.perf_counter() - t0
-        free = np.arange(2, spec.n_params)
-        pulls = (res.params[free] - truth[free]) / res.errors[free]
+        diffs, pulls, secs, calls, conv = [], [], [], [], 0
+        for t in range(n_toys):
+            lik.set_events(toys[t])
+            if t == 0:
+                for _ in range(3):
+                    lik.nll_grad(starts[t])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = fit(lik, starts[t], fixed=tuple(range(2 * R)))
+            secs.append(time.perf_counter() - t0)
+            calls.append(res.n_calls)
+            conv += int(res.converged)
+            d = res.params[knots] - truth[knots]
+            diffs.append(d)
+            pulls.append(d / res.errors[knots])
+        diffs, pulls = np.array(diffs), np.array(pulls)
+        pm, ps = pulls.mean(0), pulls.std(0, ddof=1)
+        chi2 = float(np.sum((pm / (ps / np.sqrt(n_toys))) ** 2))
+
+        def per_knot(x):
+            return {"a": [round(float(v), 4) for v in x[:N]],
+                    "phi": [round(float(v), 4) for v in x[N:]]}
         out.append({"grid_spacing_gev2": spacing, "norm_points": int(grid.shape[0]),
-                    "fit_seconds": dt, "nll_grad_calls": res.n_calls,
-                    "converged": res.converged, "edm": res.edm,
-                    "mean_abs_pull": float(np.mean(np.abs(pulls))),
-                    "max_abs_pull": float(np.max(np.abs(pulls)))})
-    return {"workload": "D+ -> K- K+ K+, phi(1020) P-wave + 40-knot S-wave, 100K toy events, FP64",
+                    "n_toys": n_toys, "converged": conv,
+                    "fit_seconds_mean": float(np.mean(secs)),
+                    "fit_seconds_max": float(np.max(secs)),
+                    "nll_grad_calls_mean": float(np.mean(calls)),
+                    "mean_pull": float(pulls.mean()),
+                    "mean_pull_error": float(pulls.std(ddof=1) / np.sqrt(pulls.size)),
+                    "pull_rms": float(np.sqrt(np.mean(pulls ** 2))),
+                    "chi2_knot_mean_pulls": chi2, "ndf": 2 * N,
+                    "diff_mean_by_knot": per_knot(diffs.mean(0)),
+                    "pull_mean_by_knot": per_knot(pm), "pull_std_by_knot": per_knot(ps)})
+    return {"workload": (f"D+ -> K- K+ K+, phi(1020) P-wave + 40-knot S-wave, {n_toys} toys of "
+                         "100K events each, FP64 fits started 0.02 from the truth, c_phi fixed"),
             "fits": out, "paper_fit_seconds": PAPER_FIT_SECONDS}
 
 
@@ -762,37 +793,47 @@ def run(args, world, rank, local, stream):
     # ---- Re/Im S-wave form: direct, and with the per-cell moment normalisation
     reim = reim_leg(args, lik, spec, params, events, stream, world) if args.reim_steps > 0 else None
 
-    # ---- end to end from pinned host buffers through the C ABI
+    # ---- end to end from pinned host buffers through the C ABI: one pipelined
+    # call per step (mipwa_nll_grad_streamed: copies in pieces, each piece
+    # checked, grouped and evaluated as it lands), and for comparison the
+    # three-call path (set_events, set_norm_sample, nll_grad)
     e2e = None
     if args.e2e_steps > 0:
         data_h = data.cpu().pin_memory()
         norm_h = norm.cpu().pin_memory()
         for _ in range(args.warmup):
-            lik.set_events(data_h)
-            lik.set_norm_sample(norm_h)
-            lik.nll_grad(params)
+            lik.nll_grad_streamed(params, data_h, norm_h)
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push("e2e")
         g0.record(stream)
-        phases = [0.0, 0.0, 0.0]  # host time in each call (each returns when its work is done)
         step_ms = []
         for _ in range(args.e2e_steps):
             t_a = time.perf_counter()
-            lik.set_events(data_h)
-            t_b = time.perf_counter()
-            lik.set_norm_sample(norm_h)
-            t_c = time.perf_counter()
-            lik.nll_grad(params)
-            t_d = time.perf_counter()
-            phases[0] += t_b - t_a
-            phases[1] += t_c - t_b
-            phases[2] += t_d - t_c
-            step_ms.append(1e3 * (t_d - t_a))
+            lik.nll_grad_streamed(params, data_h, norm_h)
+            step_ms.append(1e3 * (time.perf_counter() - t_a))
         g1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         te = max_over_ranks(g0.elapsed_time(g1), world)
+        # the three-call path on the same buffers
+        n3 = max(3, args.e2e_steps // 5)
+        for _ in range(2):
+            lik.set_events(data_h)
+            lik.set_norm_sample(norm_h)
+            lik.nll_grad(params)
+        torch.cuda.synchronize()
+        g0.record(stream)
+        step3 = []
+        for _ in range(n3):
+            t_a = time.perf_counter()
+            lik.set_events(data_h)
+            lik.set_norm_sample(norm_h)
+            lik.nll_grad(params)
+            step3.append(1e3 * (time.perf_counter() - t_a))
+        g1.record(stream)
+        torch.cuda.synchronize()
+        t3 = g0.elapsed_time(g1) / n3
         # the host link on its own: plain copies of the same pinned buffers
         scratch = torch.empty_like(data)
         h2d_gbs = []
@@ -806,17 +847,23 @@ def run(args, world, rank, local, stream):
             h2d_gbs.append(3 * buf.numel() * 4 / (g0.elapsed_time(g1) / 1e3) / 1e9)
         del scratch
         P = spec.n_params
+        h2d = int(data_h.numel() * 4 + norm_h.numel() * 4 + 8 * P)
+        floor_ms = 1e3 * (data_h.numel() * 4 / (h2d_gbs[0] * 1e9) +
+                          norm_h.numel() * 4 / (h2d_gbs[1] * 1e9))
         e2e = {"value": world * events * args.e2e_steps / (te / 1e3), "unit": "events/s",
-               "ms_per_step": te / args.e2e_steps,
-               "h2d_bytes_per_step": int(data_h.numel() * 4 + norm_h.numel() * 4 + 8 * P),
+               "ms_per_step": te / args.e2e_steps, "call": "mipwa_nll_grad_streamed",
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(8 * (1 + P) + 4 + 2 * 8),
                "host_link_gbs": {"data": h2d_gbs[0], "norm": h2d_gbs[1]},
-               "host_ms_per_call": {k: 1e3 * v / args.e2e_steps for k, v in
-                                    zip(("set_events", "set_norm_sample", "nll_grad"), phases)},
+               "copy_floor_ms": floor_ms,
+               "median_over_floor": statistics.median(step_ms) / floor_ms,
                # now and then a single step takes 2-5x longer (its host-to-device
                # copies stall); the mean above includes such steps
                "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
-                           "max": max(step_ms)}}
+                           "max": max(step_ms)},
+               "three_call_path": {"ms_per_step": t3, "steps": n3,
+                                   "step_ms_median": statistics.median(step3),
+                                   "calls": "set_events + set_norm_sample + nll_grad"}}
 
     toys = None
     if args.toys_steps > 0:
@@ -824,7 +871,7 @@ def run(args, world, rank, local, stream):
         torch.cuda.empty_cache()
         toys = toys_leg(args, stream, rank)
 
-    paper = paper_fit_leg(rank) if args.paper_fit else None
+    paper = paper_fit_leg(rank, args.paper_toys) if args.paper_fit else None
 
     cpu, accuracy = None, None
     if rank == 0 and not args.no_cpu_baseline:

@@ -223,6 +223,28 @@ int mipwa_nll(mipwa_ctx* ctx, const double* params, double* nll);
  * per event). Blocks until done. */
 int mipwa_nll_grad(mipwa_ctx* ctx, const double* params, double* nll, double* grad);
 
+/* Both samples and one NLL + gradient evaluation in one pipelined call, for
+ * inputs that arrive from host memory at every evaluation (Sec. 2: the data
+ * x_i and the normalisation sample y_j of -2 ln L). data: n_data >= 0 pairs,
+ * norm: n_norm >= 1 pairs, both HOST pointers (pageable or pinned; pinned
+ * copies run at the host link's rate) of type `dtype`, each below 2^31
+ * events. The copies run in pieces (two halves of a sample of 2^16 events
+ * or more, else one piece); as each piece lands it is checked against
+ * the Dalitz plot, grouped by spline cell on its own and evaluated, so that
+ * the GPU work of a piece overlaps the copies of the pieces after it; one last
+ * kernel combines the per-block sums. The result is -2 ln L and its gradient
+ * at `params`, as mipwa_nll_grad would give after set_events and
+ * set_norm_sample with the same samples (to rounding: the events are summed
+ * in another order). On success both samples are stored as by set_events
+ * and set_norm_sample (unweighted), each piece grouped by cell. If any event
+ * lies outside the plot: MIPWA_EOUTSIDE, *n_outside (if not NULL) the count,
+ * and the stored samples unchanged; MIPWA_ENONPOS as mipwa_nll_grad (samples
+ * stored). Needs set_model; runs with the basis cache and the moment
+ * normalisation off (else MIPWA_ESTATE). Blocks until done. */
+int mipwa_nll_grad_streamed(mipwa_ctx* ctx, const double* params, const void* data,
+                            int64_t n_data, const void* norm, int64_t n_norm, int dtype,
+                            double* nll, double* grad, int64_t* n_outside);
+
 /* Batched toys (the fit-quality test of Sec. 4: many toy samples generated
  * from the PDF and fitted). n_toys (1..MIPWA_MAX_TOYS) data samples stored
  * back to back: toy t owns events [offsets[t], offsets[t+1]) of the n_total

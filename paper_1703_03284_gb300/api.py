@@ -279,6 +279,29 @@ class Likelihood:
             g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out.value, g
 
+    def nll_grad_streamed(self, params, data, norm):
+        """Set both samples from HOST arrays (n, 2) of one dtype (pinned
+        tensors copy fastest) and evaluate -2 ln L and its gradient in one
+        pipelined call (mipwa_nll_grad_streamed)."""
+        self._follow_stream()
+        p = self._params(params)
+        dptr, nd, code_d, on_d, kd = _event_buffer(data)
+        nptr, nn, code_n, on_n, kn = _event_buffer(norm)
+        if on_d or on_n:
+            raise ValueError("nll_grad_streamed takes host arrays")
+        if nd > 0 and code_d != code_n:
+            raise ValueError("data and normalisation samples must share a dtype")
+        out = ctypes.c_double()
+        g = np.empty_like(p)
+        n_out = ctypes.c_int64(0)
+        pd = ctypes.POINTER(ctypes.c_double)
+        rc = self._lib.mipwa_nll_grad_streamed(
+            self._h, p.ctypes.data_as(pd), ctypes.c_void_p(dptr), nd, ctypes.c_void_p(nptr), nn,
+            code_n, ctypes.byref(out), g.ctypes.data_as(pd), ctypes.byref(n_out))
+        del kd, kn
+        self._check(rc, n_out.value)
+        return out.value, g
+
     def nll_grad_bw(self, params):
         """(NLL, dNLL/dparams, [dNLL/dm_r, dNLL/dGamma_r]_r) in FP64 at the
         current resonance masses and widths."""

@@ -232,31 +232,36 @@ __device__ __forceinline__ void sincos_small(float d, float* sn, float* cs) {
   *cs = fmaf(s, fmaf(s, pc, -0.5f), 1.0f);
 }
 
+// The FP32 form keeps in w.t the offset from the exact knot, s - s_j
+// (evaluated as (s - float(s_j)) - (s_j - float(s_j))), which the adjoint's
+// powers of t use; the cubics are evaluated at the exact t = s - float(s_j).
 __device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<float>& sm, float s,
                                           bool reim, SwavePart<float>& w, Cplx<float>& A) {
   w.j = segment_of(m.kn, sm.knot, s);
-  w.t = __fsub_rn(s, sm.knot[w.j]);  // exact (Sterbenz) on the knot grids used here
   const float* seg = &sm.coef[w.j * kSeg32];
   const float4* c4 = reinterpret_cast<const float4*>(seg);
-  const F2 a = cubic_hl(c4[0], c4[1], w.t);
+  const float4 k = c4[5];  // small-phase flag, float(s_j), s_j - float(s_j), unused
+  const float t = __fsub_rn(s, k.y);  // exact (Sterbenz) on the knot grids used here
+  w.t = t - k.z;
+  const F2 a = cubic_hl(c4[0], c4[1], t);
   if (reim) {
-    const F2 ph = cubic_hl(c4[2], c4[3], w.t);
+    const F2 ph = cubic_hl(c4[2], c4[3], t);
     A.re += a.hi + a.lo;
     A.im += ph.hi + ph.lo;
     return;
   }
-  if (seg[20] != 0.0f) {
+  if (k.x != 0.0f) {
     // e^{i phi} = e^{i phi_ref} e^{i delta}, delta = phi - phi_ref (the phase
     // cubic without its hi constant term; small over this segment)
     const float4 h = c4[2], l = c4[3], e = c4[4];  // e: cos phi_ref hi/lo, sin phi_ref hi/lo
-    const float tq = fmaf(fmaf(h.w, w.t, h.z), w.t, h.y) * w.t;
-    const float pl = fmaf(fmaf(fmaf(l.w, w.t, l.z), w.t, l.y), w.t, l.x);
+    const float tq = fmaf(fmaf(h.w, t, h.z), t, h.y) * t;
+    const float pl = fmaf(fmaf(fmaf(l.w, t, l.z), t, l.y), t, l.x);
     float sd, cd;
     sincos_small(tq + pl, &sd, &cd);
     w.cs = fmaf(e.x, cd, fmaf(e.y, cd, -fmaf(e.z, sd, e.w * sd)));
     w.sn = fmaf(e.z, cd, fmaf(e.w, cd, fmaf(e.x, sd, e.y * sd)));
   } else {
-    const F2 ph = cubic_hl(c4[2], c4[3], w.t);
+    const F2 ph = cubic_hl(c4[2], c4[3], t);
     sincos_cw(ph.hi, ph.lo, &w.sn, &w.cs);
   }
   w.a = a.hi;
@@ -268,7 +273,14 @@ __device__ __forceinline__ void swave_add(const Model& m, const EvalSmem<float>&
 // Forward amplitude of one event: fills the Bose-symmetrised Breit-Wigner
 // basis B[r] (FP32 form: B_r / cscale_r) and the S-wave pieces of both
 // channels. With a cached basis, B is read instead of computed.
-template <typename T, int SIG, bool CACHED>
+template <typename T, int SIG>
+__device__ __forceinline__ void basis_of(const Model& m, T s12, T s13, Cplx<T>* B) {
+  if constexpr (std::is_same<T, float>::value) bw_basis<sig_spins(SIG)>(m, s12, s13, B);
+  else bw_basis(m, s12, s13, B);
+}
+
+// PRE: B already holds the event's basis.
+template <typename T, int SIG, bool CACHED, bool PRE = false>
 __device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& sm, T s12, T s13,
                                              const Cplx<T>* cached, int64_t i, int64_t n,
                                              Cplx<T>* B, SwaveState<T>& w) {
@@ -278,10 +290,8 @@ __device__ __forceinline__ Cplx<T> amplitude(const Model& m, const EvalSmem<T>& 
 #pragma unroll
     for (int r = 0; r < NR; ++r)
       if (r < m.n_res) B[r] = cached[(int64_t)r * n + i];
-  } else if constexpr (std::is_same<T, float>::value) {
-    bw_basis<SP>(m, s12, s13, B);
-  } else {
-    bw_basis(m, s12, s13, B);
+  } else if constexpr (!PRE) {
+    basis_of<T, SIG>(m, s12, s13, B);
   }
   Cplx<T> A = combine<NR>(m, sm, B);
   // the S-wave form: at run time, or fixed by a specialised kernel's signature
@@ -304,15 +314,14 @@ __device__ __forceinline__ void bin_add(EvalSmem<T>& sm, int idx, T v) {
 // polynomial bins: d|A|^2/d a(s) = 2 Re(A* e^{i phi}) and
 // d|A|^2/d phi(s) = 2 a Re(A* i e^{i phi}) (Re/Im form: d|A|^2/dx(s) = 2 Re A,
 // d|A|^2/dy(s) = 2 Im A), times t^m, t = s - s_j (the exact knot: the FP32
-// form evaluates about float(s_j) and shifts back here). Aw = 2 wt A: the
+// form keeps that offset in w.t). Aw = 2 wt A: the
 // event's weight and the factor 2 applied once.
 template <typename T>
 __device__ __forceinline__ void swave_adjoint(const EvalSmem<T>& sm, const SwavePart<T>& w,
                                               bool reim, Cplx<T> Aw, T* v) {
   const T abar = reim ? Aw.re : Aw.re * w.cs + Aw.im * w.sn;
   const T pbar = reim ? Aw.im : w.a * (Aw.im * w.cs - Aw.re * w.sn);
-  T t1 = w.t;
-  if constexpr (std::is_same<T, float>::value) t1 = w.t - sm.knot_lo[w.j];
+  const T t1 = w.t;
   const T t2 = t1 * t1, t3 = t2 * t1;
   v[0] = abar;
   v[1] = abar * t1;
@@ -411,6 +420,29 @@ __device__ __forceinline__ void flush_bins_warp(EvalSmem<T>& sm, int cur, T (&ac
   }
 }
 
+// Column col of rows [r0, r0 + n) of a W-wide row array, in a fixed order:
+// kLanes interleaved partial sums (row r into sum r mod kLanes), which keeps
+// kLanes loads in flight, then added in lane order.
+__device__ __forceinline__ double sum_rows(const double* partials, int W, int col, int r0, int n) {
+  constexpr int kLanes = 8;
+  double acc[kLanes];
+#pragma unroll
+  for (int l = 0; l < kLanes; ++l) acc[l] = 0.0;
+  int r = 0;
+  for (; r + kLanes <= n; r += kLanes) {
+    double v[kLanes];
+#pragma unroll
+    for (int l = 0; l < kLanes; ++l) v[l] = __ldcg(&partials[(size_t)(r0 + r + l) * W + col]);
+#pragma unroll
+    for (int l = 0; l < kLanes; ++l) acc[l] += v[l];
+  }
+  for (int l = 0; r < n; ++r, ++l) acc[l] += __ldcg(&partials[(size_t)(r0 + r) * W + col]);
+  double s = 0.0;
+#pragma unroll
+  for (int l = 0; l < kLanes; ++l) s += acc[l];
+  return s;
+}
+
 // Reduce partial rows in a fixed order, then -2 ln L, its gradient and the
 // adjoint of the natural-spline solve (ybar += D^T T^{-1} Mbar). Data rows are
 // [d0, d0 + dn), normalisation rows [n0, n0 + nn); writes out[0..P] (BWG: and
@@ -424,11 +456,8 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
   const int W0 = partial_width(N, R, GRAD);
   const int W = W0 + (BWG ? 2 * R : 0);
   for (int col = threadIdx.x; col < W; col += blockDim.x) {
-    double sd = 0.0, sn = 0.0;
-    for (int row = d0; row < d0 + dn; ++row) sd += __ldcg(&partials[(size_t)row * W + col]);
-    for (int row = n0; row < n0 + nn; ++row) sn += __ldcg(&partials[(size_t)row * W + col]);
-    sm.fin_d[col] = sd;
-    sm.fin_n[col] = sn;
+    sm.fin_d[col] = sum_rows(partials, W, col, d0, dn);
+    sm.fin_n[col] = sum_rows(partials, W, col, n0, nn);
   }
   __syncthreads();
   const double S = sm.fin_n[0];
@@ -494,13 +523,15 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
 // spline polynomial adjoints (8 (N-1))]. The per-evaluation model data must be
 // staged in sm; the bins are zeroed here. Every thread of the block calls this.
 template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false,
-          bool WN = false>
+          bool WN = false, int U = 1>
 __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
                                  const Cplx<T>* cached, int64_t n, int64_t first, int64_t end,
                                  int64_t stride, bool is_data, double* row, int* flags,
                                  const double* coef64, const void* norm_w = nullptr) {
   static_assert(!BWG || (std::is_same<T, double>::value && GRAD && !CACHED && SIG == 0),
                 "mass/width derivatives: FP64, direct, with the gradient");
+  static_assert(U == 1 || !BWG, "several events per thread: not with the mass/width terms");
+  constexpr bool PRE = U > 1 && !CACHED;  // Breit-Wigner terms computed before the rest
   const int R = m.n_res, nseg = m.kn.n - 1;
   if constexpr (GRAD) {
     for (int i = threadIdx.x; i < nseg * 8; i += blockDim.x) {
@@ -537,21 +568,19 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   // (hides the global-load latency behind this iteration's arithmetic; with
   // the cached basis the extra registers cost more than they hide)
   EvT e_next{};
-  if constexpr (!CACHED) {
+  if constexpr (!CACHED && U == 1) {
     if (first + threadIdx.x < end) e_next = ev[first + threadIdx.x];
   }
-  for (int64_t base = first; base < end; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    EvT e = e_next;
-    if constexpr (!CACHED) {
-      if (i + stride < end) e_next = ev[i + stride];
-    } else {
-      if (i < end) e = ev[i];
-    }
+  // the per-event work: amplitude (B given when PRE), sums, adjoint
+  auto one = [&](const EvT& e, int64_t i, const Cplx<T>* Bpre) {
     bool ok = false;
     SwaveState<T> sw;
     Cplx<T> A{T(0), T(0)};
     Cplx<T> B[kMaxRes];
+    if constexpr (PRE) {
+#pragma unroll
+      for (int r = 0; r < kMaxRes; ++r) B[r] = Bpre[r];
+    }
     Cplx<double> dBm[BWG ? kMaxRes : 1], dBw[BWG ? kMaxRes : 1];
     T wt = T(1);
     if (i < end) {
@@ -562,7 +591,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
         swave_add(m, sm, s12, m.reim != 0, sw.c12, A);
         swave_add(m, sm, s13, m.reim != 0, sw.c13, A);
       } else {
-        A = amplitude<T, SIG, CACHED>(m, sm, s12, s13, cached, i, n, B, sw);
+        A = amplitude<T, SIG, CACHED, PRE>(m, sm, s12, s13, cached, i, n, B, sw);
       }
       const T A2 = A.re * A.re + A.im * A.im;
       if (is_data) {
@@ -651,6 +680,38 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
         }
         __syncthreads();
       }
+    }
+  };
+  if constexpr (U == 1) {
+    for (int64_t base = first; base < end; base += stride) {
+      const int64_t i = base + threadIdx.x;
+      EvT e = e_next;
+      if constexpr (!CACHED) {
+        if (i + stride < end) e_next = ev[i + stride];
+      } else {
+        if (i < end) e = ev[i];
+      }
+      one(e, i, nullptr);
+    }
+  } else {
+    // U events per thread per iteration; with computed Breit-Wigner terms the
+    // U bases are evaluated back to back (independent chains the scheduler
+    // can interleave), an event past the end standing in as the first one
+    for (int64_t base = first; base < end; base += stride * U) {
+      EvT e[U];
+      int64_t ii[U];
+      Cplx<T> Bp[U][kMaxRes];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        ii[u] = base + u * stride + threadIdx.x;
+        e[u] = ev[ii[u] < end ? ii[u] : first];
+      }
+      if constexpr (PRE) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) basis_of<T, SIG>(m, (T)e[u].x, (T)e[u].y, Bp[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) one(e[u], ii[u], Bp[u]);
     }
   }
   if (bad) atomicOr(flags, is_data ? kFlagData : kFlagNorm);

@@ -73,7 +73,9 @@ struct mipwa_ctx {
   // overlaps the previous sample's sort on the context stream
   cudaStream_t copy_stream = nullptr;
   static constexpr int kCopyPieces = 8;  // a sorted sample arrives in pieces, each counted on arrival
-  cudaEvent_t piece_done[kCopyPieces] = {};
+  cudaEvent_t piece_done[2 * kCopyPieces] = {};  // streamed call: data pieces, then norm pieces
+  void* d_stream_tmp = nullptr;  // streamed call: the sort's middle buffer for one piece at a time
+  size_t stream_tmp_cap = 0;
   bool basis_on = false;
   // Re/Im form: normalisation from per-cell moments of the normalisation sample
   bool gram_on = false;
@@ -361,9 +363,16 @@ void invalidate_basis(mipwa_ctx* c) {
 
 // Per-cell moments of the normalisation sample for the current model (Re/Im
 // form): cell ranges of the grouped sample, then one block per cell.
+int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp);
+
 int build_gram(mipwa_ctx* c) {
   if (c->gram_valid) return MIPWA_OK;
   auto& smp = c->norm;
+  if (!smp.sorted && sortable(smp.n)) {
+    // grouped piece by piece only (mipwa_nll_grad_streamed): group it whole
+    const int rc = resort(c, smp);
+    if (rc) return rc;
+  }
   if (!(smp.sorted || smp.n == 1))
     return fail(c, MIPWA_EINVAL, "the moment normalisation needs a sample of fewer than 2^31 events");
   const int nseg = c->model.kn.n - 1, nkeys = nseg * nseg;
@@ -911,6 +920,189 @@ int run_toys(mipwa_ctx* c) {
   return MIPWA_OK;
 }
 
+// The streamed call takes a sample in kStreamPieces pieces, each grouped and
+// evaluated on its own, and copies each piece in kStreamSub sub-pieces
+// (halving), each counted (the sort's first pass and the Dalitz check) as it
+// lands. 2 x 4 = kCopyPieces copy events per sample.
+constexpr int kStreamPieces = 2;
+constexpr int kStreamSub = 4;
+
+// One pipelined call: copy both samples from host memory in pieces and, as
+// each piece lands, check it against the Dalitz plot, group it by spline
+// cell (the piece sorted on its own) and evaluate its events into partial
+// rows; one last kernel combines the rows. The GPU work of a piece overlaps
+// the copies of the pieces after it.
+int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n_data,
+                 const void* norm, int64_t n_norm, int dtype, double* nll, double* grad,
+                 int64_t* n_outside) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (n_outside) *n_outside = 0;
+  if (!params || !nll || !grad || !norm || (n_data > 0 && !data))
+    return fail(c, MIPWA_EINVAL, "null pointer");
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  if (dtype != MIPWA_F32 && dtype != MIPWA_F64) return fail(c, MIPWA_EINVAL, "bad dtype %d", dtype);
+  if (n_data < 0 || n_norm < 1 || n_data >= (int64_t)0x7fffffff || n_norm >= (int64_t)0x7fffffff)
+    return fail(c, MIPWA_EINVAL, "event counts must be in 0..2^31-1 (data), 1..2^31-1 (norm)");
+  if ((n_data > 0 && is_copy_source(data)) || is_copy_source(norm))
+    return fail(c, MIPWA_EINVAL, "the streamed call takes host pointers");
+  if (c->basis_on || c->gram_on)
+    return fail(c, MIPWA_ESTATE, "the streamed call runs with the basis cache and the moment "
+                                 "normalisation off");
+  const int P = c->n_params;
+  for (int k = 0; k < P; ++k)
+    if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
+  const int f32 = c->mode == MIPWA_F32, ev32 = dtype == MIPWA_F32;
+  const size_t eb = ev_bytes(dtype);
+  const int total = c->sm_count * eval_blocks_per_sm(f32, ev32, c->model, false, false);
+  const int W = partial_width(c->model.kn.n, c->model.n_res, true);
+  static_assert(kStreamPieces * kStreamSub == mipwa_ctx::kCopyPieces, "copy events");
+  mipwa_ctx::Sample* smp[2] = {&c->data, &c->norm};
+  const void* src[2] = {data, norm};
+  const int64_t nev[2] = {n_data, n_norm};
+  // pieces of a sample: two halves from 2^16 events up, one piece below
+  // (each piece costs its sort and its evaluation a fixed ~0.3 ms on GB300;
+  // two halves keep the GPU work of a step close to its copy time)
+  int pieces[2];
+  int64_t bounds[2][mipwa_ctx::kCopyPieces + 1];
+  size_t rows_cap = 0;
+  for (int s = 0; s < 2; ++s) {
+    pieces[s] = nev[s] >= (1 << 16) ? kStreamPieces : 1;
+    for (int p = 0; p <= pieces[s]; ++p) bounds[s][p] = sort_piece_begin(nev[s], p, pieces[s]);
+    for (int p = 0; p < pieces[s]; ++p) {
+      const int64_t np = bounds[s][p + 1] - bounds[s][p];
+      rows_cap += (size_t)std::min<int64_t>(total, (np + kThreads - 1) / kThreads);
+    }
+  }
+  for (int s = 0; s < 2; ++s) {
+    rc = ensure(c, &smp[s]->spare, &smp[s]->spare_cap, (size_t)nev[s] * eb);
+    if (rc) return rc;
+  }
+  rc = ensure(c, &c->d_stream_tmp, &c->stream_tmp_cap, (size_t)std::max(n_data, n_norm) * eb);
+  if (!rc) rc = ensure_sortwork(c);
+  if (!rc) rc = ensure(c, (void**)&c->d_partials, &c->partials_cap,
+                       std::max<size_t>(rows_cap, 1) * W * sizeof(double));
+  if (rc) return rc;
+  // parameters and spline setup first (the pieces' evaluations need them)
+  std::memcpy(c->h_stage, params, P * sizeof(double));
+  CK(c, cudaMemcpyAsync(c->d_params, c->h_stage, P * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
+  CK(c, cudaMemsetAsync(c->d_count, 0, 2 * sizeof(unsigned long long), c->stream));
+  launch_prepare(c->model, c->d_params, c->d_lu, c->d_coef, c->d_coef32, c->stream);
+  CK(c, cudaGetLastError());
+  c->launches++;
+  // every copy on the copy stream, each spare buffer once the kernels that
+  // last read it are done
+  for (int s = 0; s < 2; ++s) {
+    CK(c, cudaStreamWaitEvent(c->copy_stream, smp[s]->spare_free, 0));
+    for (int p = 0; p < pieces[s]; ++p) {
+      const int64_t e0 = bounds[s][p], e1 = bounds[s][p + 1];
+      for (int q = 0; q < kStreamSub; ++q) {
+        const int64_t np = e1 - e0;
+        const int64_t q0 = e0 + sort_piece_begin(np, q, kStreamSub);
+        const int64_t q1 = e0 + sort_piece_begin(np, q + 1, kStreamSub);
+        if (q1 > q0)
+          CK(c, cudaMemcpyAsync((char*)smp[s]->spare + q0 * eb, (const char*)src[s] + q0 * eb,
+                                (q1 - q0) * eb, cudaMemcpyHostToDevice, c->copy_stream));
+        CK(c, cudaEventRecord(c->piece_done[(s * kStreamPieces + p) * kStreamSub + q],
+                              c->copy_stream));
+      }
+    }
+  }
+  EvalArgs a;
+  a.n_params = P;
+  a.coef = c->d_coef;
+  a.coef32 = c->d_coef32;
+  a.lu = c->d_lu;
+  a.partials = c->d_partials;
+  a.counter = c->d_counter;
+  a.out = c->d_out;
+  a.flags = c->d_flags;
+  a.basis_data = a.basis_norm = nullptr;
+  a.model = c->model;
+  a.norm_w = nullptr;
+  a.norm_count = 0.0;
+  a.finalize = 0;
+  int rows[2] = {0, 0};
+  for (int s = 0; s < 2; ++s) {
+    for (int p = 0; p < pieces[s]; ++p) {
+      const int64_t e0 = bounds[s][p], np = bounds[s][p + 1] - e0;
+      char* piece = (char*)smp[s]->spare + e0 * eb;
+      for (int q = 0; q < kStreamSub; ++q) {
+        CK(c, cudaStreamWaitEvent(c->stream,
+                                  c->piece_done[(s * kStreamPieces + p) * kStreamSub + q], 0));
+        if (np > 0) {
+          CK(c, launch_sort_count_checked(ev32, c->model, piece, np, c->d_sortwork,
+                                          c->d_count + s, c->stream, q, kStreamSub));
+          c->launches++;
+        }
+      }
+      if (np == 0) continue;
+      if (sortable(np)) {
+        CK(c, launch_sort_rest(ev32, c->model, piece, np, c->d_stream_tmp, piece, c->d_sortwork,
+                               c->stream));
+        c->launches += kSortLaunches - 1;
+      }
+      const int nb = (int)std::min<int64_t>(total, (np + kThreads - 1) / kThreads);
+      a.data = s == 0 ? piece : nullptr;
+      a.norm = s == 1 ? piece : nullptr;
+      a.n_data = s == 0 ? np : 0;
+      a.n_norm = s == 1 ? np : 0;
+      a.nb_data = s == 0 ? nb : 0;
+      a.nb_norm = s == 1 ? nb : 0;
+      a.row0 = rows[0] + rows[1];
+      CK(c, launch_eval(f32, ev32, true, a, nb, c->stream));
+      c->launches++;
+      rows[s] += nb;
+    }
+  }
+  a.n_data = n_data;
+  a.n_norm = n_norm;
+  CK(c, launch_finalize(f32, true, a, rows[0], rows[1], c->stream));
+  c->launches++;
+  // the buffers this call read are free for the next copies once this is done
+  for (int s = 0; s < 2; ++s) CK(c, cudaEventRecord(smp[s]->spare_free, c->stream));
+  double* h_out = c->h_stage + kParamsMax;
+  int* h_flags = (int*)(h_out + 1 + P);
+  unsigned long long* h_outside = reinterpret_cast<unsigned long long*>(c->h_stage + kSetBack);
+  CK(c, cudaMemcpyAsync(h_out, c->d_out, (1 + P) * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaMemcpyAsync(h_flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(h_outside, c->d_count, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const unsigned long long outside = h_outside[0] + h_outside[1];
+  if (outside > 0) {
+    if (n_outside) *n_outside = (int64_t)outside;
+    return fail(c, MIPWA_EOUTSIDE, "%llu data and %llu normalisation events lie outside the "
+                                   "Dalitz plot", h_outside[0], h_outside[1]);
+  }
+  // both samples are valid: they become the stored samples (each piece
+  // grouped by cell)
+  for (int s = 0; s < 2; ++s) {
+    mipwa_ctx::Sample& m = *smp[s];
+    std::swap(m.cur, m.spare);
+    std::swap(m.cur_cap, m.spare_cap);
+    m.n = nev[s];
+    m.dtype = dtype;
+    m.set = true;
+    m.sorted = pieces[s] == 1;  // else grouped by cell piece by piece, not as a whole
+    m.weighted = false;
+    m.wsum = (double)nev[s];
+    m.basis_valid = false;
+  }
+  c->gram_valid = false;
+  invalidate_graph(c);
+  if (*h_flags & kFlagData)
+    return fail(c, MIPWA_ENONPOS, "|A|^2 <= 0 or non-finite for a data event");
+  if (*h_flags & (kFlagNorm | kFlagIntegral) || !std::isfinite(h_out[0]))
+    return fail(c, MIPWA_ENONPOS, "normalisation integral is not positive and finite");
+  *nll = h_out[0];
+  std::memcpy(grad, h_out + 1, P * sizeof(double));
+  return MIPWA_OK;
+}
+
 // Key of the autotuner's choice: what decides the work list and the kernel
 // (model signature, forms, compute mode, event dtype, sample sizes, SMs).
 std::string tune_key(const mipwa_ctx* c) {
@@ -1082,7 +1274,7 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
       cudaMalloc(&c->d_out, kOutMax * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_counter, sizeof(unsigned int)) != cudaSuccess ||
-      cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&c->d_count, 2 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&c->d_wsum, kWeightSumDoubles * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&c->h_stage, kStage * sizeof(double)) != cudaSuccess)
     return bail(MIPWA_ENOMEM);
@@ -1114,7 +1306,8 @@ void mipwa_destroy(mipwa_ctx* c) {
                   (void*)c->d_partials, (void*)c->d_sortwork, c->data.basis, c->norm.basis,
                   (void*)c->d_cells, (void*)c->d_gram,
                   c->data.cur, c->data.spare, c->norm.cur,
-                  c->norm.spare, c->norm.w_cur, c->norm.w_spare, (void*)c->d_wsum})
+                  c->norm.spare, c->norm.w_cur, c->norm.w_spare, (void*)c->d_wsum,
+                  c->d_stream_tmp})
     if (p) cudaFree(p);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   invalidate_graph(c);
@@ -1311,6 +1504,12 @@ int mipwa_nll(mipwa_ctx* c, const double* params, double* nll) {
 
 int mipwa_nll_grad(mipwa_ctx* c, const double* params, double* nll, double* grad) {
   return evaluate(c, params, nll, grad, true);
+}
+
+int mipwa_nll_grad_streamed(mipwa_ctx* c, const double* params, const void* data,
+                            int64_t n_data, const void* norm, int64_t n_norm, int dtype,
+                            double* nll, double* grad, int64_t* n_outside) {
+  return run_streamed(c, params, data, n_data, norm, n_norm, dtype, nll, grad, n_outside);
 }
 
 int mipwa_set_toys(mipwa_ctx* c, const void* ptr, int64_t n_total, int dtype, int on_device,

@@ -28,6 +28,12 @@ namespace mipwa {
 template <typename T, bool GRAD, bool CACHED>
 constexpr int kEvalMinBlocks = sizeof(T) == 4 ? (GRAD && !CACHED ? 3 : 4) : 1;
 
+// Events per thread per loop iteration of the FP32 NLL + gradient kernels
+// with computed Breit-Wigner terms (accumulate_range's U).
+constexpr int kEvalUnroll = 1;
+template <typename T, bool GRAD, bool CACHED, bool BWG>
+constexpr int kEvalU = sizeof(T) == 4 && GRAD && !CACHED && !BWG ? kEvalUnroll : 1;
+
 // WN: the normalisation events carry weights (a.norm_w).
 template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false,
           bool WN = false>
@@ -49,10 +55,10 @@ __global__ void __launch_bounds__(kThreads, (kEvalMinBlocks<T, GRAD, CACHED>))
   const int64_t chunk = ((n + nb - 1) / nb + kThreads - 1) / kThreads * kThreads;
   const int64_t c0 = (int64_t)b * chunk;
   const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
-  accumulate_range<T, EvT, GRAD, SIG, CACHED, BWG, WN>(sm, m, ev, cached, n, c0, c1,
-                                                       (int64_t)kThreads, is_data,
-                                                       a.partials + (size_t)blockIdx.x * W,
-                                                       a.flags, a.coef, a.norm_w);
+  accumulate_range<T, EvT, GRAD, SIG, CACHED, BWG, WN, kEvalU<T, GRAD, CACHED, BWG>>(
+      sm, m, ev, cached, n, c0, c1, (int64_t)kThreads, is_data,
+      a.partials + (size_t)(a.row0 + (int)blockIdx.x) * W, a.flags, a.coef, a.norm_w);
+  if (!a.finalize) return;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -66,6 +72,27 @@ __global__ void __launch_bounds__(kThreads, (kEvalMinBlocks<T, GRAD, CACHED>))
                               a.n_data, a.norm_count > 0.0 ? a.norm_count : (double)a.n_norm,
                               a.out, a.flags);
   if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// The combine step alone, for rows written by launches without finalize.
+template <typename T, bool GRAD>
+__global__ void __launch_bounds__(kThreads) finalize_kernel(const EvalArgs a, int rows_d,
+                                                            int rows_n) {
+  __shared__ SmemCommon sm;
+  finalize_rows<T, GRAD>(sm, a.model, a.lu, a.partials, 0, rows_d, rows_d, rows_n, a.n_data,
+                         a.norm_count > 0.0 ? a.norm_count : (double)a.n_norm, a.out, a.flags);
+}
+
+cudaError_t launch_finalize(int compute_f32, bool grad, const EvalArgs& a, int rows_d, int rows_n,
+                            cudaStream_t st) {
+  if (compute_f32) {
+    if (grad) finalize_kernel<float, true><<<1, kThreads, 0, st>>>(a, rows_d, rows_n);
+    else finalize_kernel<float, false><<<1, kThreads, 0, st>>>(a, rows_d, rows_n);
+  } else {
+    if (grad) finalize_kernel<double, true><<<1, kThreads, 0, st>>>(a, rows_d, rows_n);
+    else finalize_kernel<double, false><<<1, kThreads, 0, st>>>(a, rows_d, rows_n);
+  }
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------- |A|^2 per event

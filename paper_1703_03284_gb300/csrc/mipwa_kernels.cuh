@@ -33,6 +33,10 @@ struct EvalArgs {
   // and the normalising count: sum of the weights (0: n_norm)
   const void* norm_w = nullptr;
   double norm_count = 0.0;
+  // block b writes row row0 + b; with finalize 0 no block combines the rows
+  // (launch_finalize does, after every launch that writes them)
+  int row0 = 0;
+  int finalize = 1;
 };
 
 enum { kFlagData = 1, kFlagNorm = 2, kFlagIntegral = 4 };
@@ -85,6 +89,11 @@ int toys_blocks_per_sm(int compute_f32, int ev_f32, bool cached, bool weighted, 
                        int block);
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t stream);
+// -2 ln L (and its gradient) from rows_d data rows at a.partials followed by
+// rows_n normalisation rows, with a.n_data data events and a.norm_count (0:
+// a.n_norm) normalisation weight; one block.
+cudaError_t launch_finalize(int compute_f32, bool grad, const EvalArgs& a, int rows_d, int rows_n,
+                            cudaStream_t stream);
 // FP64 NLL + gradient + d/d(m_r, Gamma_r) (no cached basis, direct
 // normalisation); rows are partial_width() + 2R wide, out holds 1 + P + 2R.
 cudaError_t launch_eval_bw(int ev_f32, const EvalArgs& a, int grid, cudaStream_t stream);

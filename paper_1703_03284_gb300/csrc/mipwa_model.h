@@ -105,8 +105,8 @@ MIPWA_HD inline int coef_size(int n_knots, int n_res) { return 8 * (n_knots - 1)
 // exact), then cos and sin of phi_ref = the phase cubic's hi constant term as
 // pairs (cos hi, cos lo, sin hi, sin lo), then 1 if the phase stays within
 // kSmallPhase of phi_ref over every t the segment's events can have (else 0),
-// and 3 unused; followed by 4 floats per resonance: (Re c'_r hi, lo,
-// Im c'_r hi, lo), c'_r = c_r cscale_r.
+// float(s_j), s_j - float(s_j) and 1 unused; followed by 4 floats per
+// resonance: (Re c'_r hi, lo, Im c'_r hi, lo), c'_r = c_r cscale_r.
 constexpr int kSeg32 = 24;
 constexpr double kSmallPhase = 0.3;
 MIPWA_HD inline int coef32_size(int n_knots, int n_res) {

@@ -93,7 +93,10 @@ __global__ void prepare_kernel(const Model m, const double* __restrict__ params,
       const double dmax = fabs(b[0] - ref) + fabs(b[1]) * tmax + fabs(b[2]) * tmax * tmax +
                           fabs(b[3]) * tmax * tmax * tmax;
       e[4] = dmax <= kSmallPhase ? 1.0f : 0.0f;
-      e[5] = e[6] = e[7] = 0.0f;
+      // the segment's knot as float(s_j) and its low part s_j - float(s_j)
+      e[5] = (float)m.kn.s[j];
+      e[6] = (float)(m.kn.s[j] - (double)e[5]);
+      e[7] = 0.0f;
     }
   }
   for (int k = threadIdx.x; k < 2 * n_res; k += blockDim.x) coef[8 * nseg + k] = params[k];
