@@ -71,10 +71,10 @@ def _measured_hbm_gbs() -> float:
 
 HBM_GBS = _measured_hbm_gbs()
 # DRAM bytes (read + write) of the fused FP32 NLL+gradient kernel per event
-# processed, from one ncu capture on 2e7 + 2e7 events (324.31 MB per launch);
-# a launch's traffic is this times its events. None once the kernel has
-# changed since the capture.
-TRAFFIC_PER_EVENT = None
+# processed, from one ncu capture on 2e7 + 2e7 events (320.45 MB read + 4.01
+# MB written per launch); a launch's traffic is this times its events. None
+# once the kernel has changed since the capture.
+TRAFFIC_PER_EVENT = (320.449536e6 + 4.005888e6) / 4e7
 
 
 def parse():
@@ -442,6 +442,10 @@ def toys_leg(args, stream, rank):
             ev_done += int(sizes[t]) + args.toys_norm
         loop[name] = {"toys_per_s": 1e3 * 4 / t_done, "event_pairs_per_s": ev_done / (t_done / 1e3),
                       "note": "4 toys timed one by one, same events"}
+    # the same toys' forward normalisation integrals with the spline values
+    # from the tensor cores, checked on 16 toys against the library's FP64
+    # |A|^2 over the same stored events
+    tc = toys_tc_leg(args, lik, spec, params, sizes, stream)
     # the same toys with the Re/Im form and the moment normalisation
     lik.set_swave_form("reim")
     lik.enable_norm_gram(True)
@@ -473,7 +477,46 @@ def toys_leg(args, stream, rank):
             "loop_single_toy": loop,
             "speedup_vs_fp64_loop": (1e3 * args.n_toys / t_ms) / loop["fp64"]["toys_per_s"],
             "dtype": "f32 (cached basis, CUDA graph)",
+            "tensor_core_norm_integrals": tc,
             "reim_moments": reim}
+
+
+def toys_tc_leg(args, lik, spec, params, sizes, stream):
+    """mipwa_toys_norm_tc on the batched toys: the kernel's time per
+    iteration (forward integrals of all toys), the error of the integrals
+    against FP64, and the -2 ln L shift that error would cause in each toy
+    (2 N_t dI/I)."""
+    import numpy as np
+    import torch
+
+    from paper_1703_03284_gb300 import F64, Likelihood
+
+    n_toys = len(params)
+    lik.toys_norm_tc(params)  # builds the cached basis tiles
+    torch.cuda.synchronize()
+    ms_call = []
+    for _ in range(max(3, args.toys_steps)):
+        I_tc, ms = lik.toys_norm_tc(params)
+        ms_call.append(ms)
+    stored = lik.stored_sample("norm")
+    ref = Likelihood(torch.cuda.current_device(), F64)
+    ref.set_spec(spec)
+    rel, dnll = [], []
+    for t in range(0, n_toys, max(1, n_toys // 16)):
+        I64 = float(ref.amp2(params[t], stored).double().mean())
+        r = (I_tc[t] - I64) / I64
+        rel.append(r)
+        dnll.append(2.0 * float(sizes[t]) * r)
+    del ref
+    kms = statistics.median(ms_call)
+    pairs = n_toys * int(stored.shape[0])
+    return {"kernel_ms": kms, "event_toy_pairs_per_s": pairs / (kms / 1e3),
+            "I_rel_err_max": float(np.max(np.abs(rel))), "I_rel_err_mean": float(np.mean(rel)),
+            "nll_shift_max": float(np.max(np.abs(dnll))), "toys_checked": len(rel),
+            "note": ("forward integrals only (no gradient): spline values a(s), phi(s) of both "
+                     "channels from tcgen05.mma (bf16 operands in three parts, FP32 accumulation "
+                     "in tensor memory), the rest of |A|^2 on the CUDA cores"),
+            "cached_basis_bytes": -(-int(stored.shape[0]) // 64) * 24576}
 
 
 def to_reim(spec, p):

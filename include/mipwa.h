@@ -71,7 +71,7 @@ typedef enum {
   MIPWA_EOUTSIDE = -2, /* an event lies outside the Dalitz plot; nothing stored */
   MIPWA_ENONPOS = -3,  /* |A|^2 <= 0 or non-finite for a data event, or I <= 0 */
   MIPWA_ECUDA = -4,    /* a CUDA runtime call failed (message in last_error) */
-  MIPWA_ETIMEOUT = -5, /* reserved: no call returns it (no kernel here waits on the device) */
+  MIPWA_ETIMEOUT = -5, /* a bounded device wait gave up (mipwa_toys_norm_tc) */
   MIPWA_ESTATE = -6,   /* call order: model / events / normalisation not set */
   MIPWA_ENOMEM = -7    /* device or pinned host allocation failed */
 } mipwa_status;
@@ -299,6 +299,26 @@ int mipwa_toys_autotune(mipwa_ctx* ctx, const double* params, mipwa_toys_config*
  * blocks_per_sm" line each: mipwa_toys_autotune looks a key up there (the last
  * matching line wins) and appends each new choice. NULL or "" turns it off. */
 int mipwa_set_toys_tune_file(mipwa_ctx* ctx, const char* path);
+
+/* Forward normalisation integrals of every toy, I_t = (1/N_norm) sum_j
+ * |A_t(y_j)|^2 over the normalisation sample (Sec. 2; the batched fits of
+ * Sec. 4), with the S-wave spline values a_t(s), phi_t(s) of both channels
+ * computed on the tensor cores (sm_103a tcgen05.mma, bf16 operands split in
+ * three parts, FP32 accumulation in tensor memory): the knot values of 128
+ * toys at a time times the cardinal spline basis of 64 events at a time,
+ * cached once per normalisation sample and knots (0.6 KB per event). The
+ * rest of |A|^2 (c_r B_r from the basis cache, e^{i phi}, the sums) runs on
+ * the CUDA cores. A measurement path beside the CUDA-core batched evaluation
+ * (no gradient). Needs set_toys and a normalisation sample of float32 events
+ * in FP32 compute mode, magnitude/phase S-wave of at most 32 knots, the basis
+ * cache on, no weights and no moment normalisation (else MIPWA_ESTATE or
+ * MIPWA_EINVAL). params: n_toys * P host doubles. mode 0: out receives n_toys
+ * integrals; mode 1: out receives the four spline products of the first 64
+ * events for the first 128 toys, [a(s12), phi(s12), a(s13), phi(s13)][toy]
+ * [event] (4 x 128 x 64 doubles; toys past n_toys are 0). *ms (if not NULL):
+ * the kernel's duration. MIPWA_ETIMEOUT if a completion wait of the kernel
+ * gave up (after about a second). Blocks. */
+int mipwa_toys_norm_tc(mipwa_ctx* ctx, const double* params, int mode, double* out, double* ms);
 
 /* Capture the batched evaluation in a CUDA graph (on != 0, the default) or
  * launch its kernels one by one. */

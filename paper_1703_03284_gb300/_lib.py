@@ -62,6 +62,7 @@ SIGNATURES = [
     ("mipwa_nll_grad_toys", _i, [_vp, _pd, _pd, _pd]),
     ("mipwa_toys_autotune", _i, [_vp, _pd, ctypes.POINTER(ToysConfig), ctypes.POINTER(_i)]),
     ("mipwa_set_toys_graph", _i, [_vp, _i]),
+    ("mipwa_toys_norm_tc", _i, [_vp, _pd, _i, _pd, _pd]),
     ("mipwa_set_toys_config", _i, [_vp, ctypes.POINTER(ToysConfig)]),
     ("mipwa_get_toys_config", _i, [_vp, ctypes.POINTER(ToysConfig)]),
     ("mipwa_set_toys_tune_file", _i, [_vp, ctypes.c_char_p]),

@@ -231,6 +231,21 @@ class Likelihood:
         out["n_timed"] = n_timed.value
         return out
 
+    def toys_norm_tc(self, params, mode: int = 0):
+        """mipwa_toys_norm_tc: (integrals per toy, kernel ms) for mode 0, or
+        (the spline products [4, 128, 64] of the first tile, kernel ms) for
+        mode 1."""
+        self._follow_stream()
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        if p.shape != (self.n_toys, self.n_params):
+            raise ValueError(f"expected params of shape {(self.n_toys, self.n_params)}")
+        out = np.zeros(self.n_toys if mode == 0 else 4 * 128 * 64)
+        ms = ctypes.c_double(0.0)
+        pd = ctypes.POINTER(ctypes.c_double)
+        self._check(self._lib.mipwa_toys_norm_tc(self._h, p.ctypes.data_as(pd), int(mode),
+                                                 out.ctypes.data_as(pd), ctypes.byref(ms)))
+        return (out if mode == 0 else out.reshape(4, 128, 64)), ms.value
+
     def set_toys_graph(self, on: bool = True):
         self._check(self._lib.mipwa_set_toys_graph(self._h, int(bool(on))))
 

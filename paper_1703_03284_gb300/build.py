@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmipwa.so")
 SOURCES = ["mipwa_api.cu", "mipwa_eval.cu", "mipwa_spline.cu", "mipwa_sort.cu", "mipwa_toys.cu",
-           "mipwa_noalloc.cu", "mipwa_gram.cu", "mipwa_probe.cu"]
+           "mipwa_noalloc.cu", "mipwa_gram.cu", "mipwa_probe.cu", "mipwa_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

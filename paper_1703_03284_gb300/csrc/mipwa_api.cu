@@ -42,6 +42,7 @@ struct mipwa_ctx {
   double* d_wsum = nullptr;  // sum of a new sample's weights (kWeightSumDoubles)
   double* d_partials = nullptr;
   size_t partials_cap = 0;  // doubles
+  double* d_rows2 = nullptr;  // the column sums of the data and normalisation rows (2 x W)
   int* d_sortwork = nullptr;
   size_t sortwork_cap = 0;  // bytes
   double* h_stage = nullptr;  // pinned: params in, results out
@@ -68,7 +69,22 @@ struct mipwa_ctx {
     size_t w_spare_cap = 0;
     bool weighted = false;
     double wsum = 0.0;
+    uint64_t gen = 0;  // bumped whenever the stored events change
   } data, norm, toys;
+  uint64_t model_gen = 0;  // bumped by set_model
+  // tensor-core normalisation integrals: cached basis tiles of the
+  // normalisation sample (for norm.gen, model_gen) and per-call buffers
+  uint8_t* d_tc_tiles = nullptr;
+  size_t tc_tiles_cap = 0;
+  double* d_tc_dmdy = nullptr;
+  uint4* d_tc_theta = nullptr;
+  size_t tc_theta_cap = 0;
+  float* d_tc_cr = nullptr;
+  size_t tc_cr_cap = 0;
+  double* d_tc_partial = nullptr;
+  size_t tc_partial_cap = 0;
+  float* d_tc_dump = nullptr;
+  uint64_t tc_norm_gen = ~0ull, tc_model_gen = ~0ull;
   // host-to-device copies of new samples run here, so that one sample's copy
   // overlaps the previous sample's sort on the context stream
   cudaStream_t copy_stream = nullptr;
@@ -135,6 +151,7 @@ namespace {
 // results [NLL, gradient (P), resonance derivatives (2R)], then the flags.
 constexpr int kParamsMax = 2 * kMaxRes + 2 * kMaxKnots;
 constexpr int kOutMax = 1 + kParamsMax + 2 * kMaxRes;
+constexpr int kRowMax = 1 + 2 * kMaxRes + 8 * kMaxSeg + 2 * kMaxRes;  // widest partial row
 // pinned staging: parameters, results (+ flags), then set_sample's read-backs
 constexpr int kSetBack = kParamsMax + kOutMax + 1;  // outside count, weight sum, bad weights
 constexpr int kStage = kSetBack + 3;
@@ -545,6 +562,7 @@ int set_sample(mipwa_ctx* c, mipwa_ctx::Sample& smp, const void* ptr, int64_t n,
   smp.n = n;
   smp.dtype = dtype;
   smp.set = true;
+  smp.gen++;
   smp.basis_valid = false;
   invalidate_graph(c);
   return MIPWA_OK;
@@ -567,6 +585,7 @@ int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
   CK(c, cudaEventRecord(smp.spare_free, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   smp.sorted = true;
+  smp.gen++;
   smp.basis_valid = false;
   return MIPWA_OK;
 }
@@ -665,9 +684,16 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
                            c->d_partials + (size_t)nb_d * W, nseg, 1, c->stream));
     c->launches++;
   }
+  // the event kernel writes one row per block; the rows are combined by many
+  // blocks in a fixed order, then one block forms -2 ln L and the gradient
+  a.finalize = 0;
   CK(c, launch_eval(f32, ev32, want_grad, a, grid, c->stream));
+  CK(c, launch_reduce_rows(c->d_partials, W, nb_d, rows - nb_d, c->d_rows2, c->stream));
+  EvalArgs fa = a;
+  fa.partials = c->d_rows2;
+  CK(c, launch_finalize(f32, want_grad, fa, 1, 1, c->stream));
   if (c->timing) CK(c, cudaEventRecord(c->ev1, c->stream));
-  c->launches += 2;
+  c->launches += 4;
   double* h_out = c->h_stage + kParamsMax;
   int* h_flags = (int*)(h_out + 1 + P);
   CK(c, cudaMemcpyAsync(h_out, c->d_out, (1 + (want_grad ? P : 0)) * sizeof(double),
@@ -1059,8 +1085,10 @@ int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n
   }
   a.n_data = n_data;
   a.n_norm = n_norm;
-  CK(c, launch_finalize(f32, true, a, rows[0], rows[1], c->stream));
-  c->launches++;
+  CK(c, launch_reduce_rows(c->d_partials, W, rows[0], rows[1], c->d_rows2, c->stream));
+  a.partials = c->d_rows2;
+  CK(c, launch_finalize(f32, true, a, 1, 1, c->stream));
+  c->launches += 2;
   // the buffers this call read are free for the next copies once this is done
   for (int s = 0; s < 2; ++s) CK(c, cudaEventRecord(smp[s]->spare_free, c->stream));
   double* h_out = c->h_stage + kParamsMax;
@@ -1088,6 +1116,7 @@ int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n
     m.dtype = dtype;
     m.set = true;
     m.sorted = pieces[s] == 1;  // else grouped by cell piece by piece, not as a whole
+    m.gen++;
     m.weighted = false;
     m.wsum = (double)nev[s];
     m.basis_valid = false;
@@ -1100,6 +1129,168 @@ int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n
     return fail(c, MIPWA_ENONPOS, "normalisation integral is not positive and finite");
   *nll = h_out[0];
   std::memcpy(grad, h_out + 1, P * sizeof(double));
+  return MIPWA_OK;
+}
+
+// bf16 of a float, rounded to nearest even (finite values).
+uint16_t bf16_bits(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  return (uint16_t)(b >> 16);
+}
+double bf16_value(uint16_t v) {
+  const uint32_t b = (uint32_t)v << 16;
+  float f;
+  std::memcpy(&f, &b, 4);
+  return (double)f;
+}
+
+// The forward normalisation integrals of every toy, I_t = (1/N) sum_j |A_t(y_j)|^2,
+// with the spline values from the tensor cores (mipwa_toys_norm_tc).
+int run_toys_norm_tc(mipwa_ctx* c, const double* params, int mode, double* out, double* ms) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!params || !out) return fail(c, MIPWA_EINVAL, "null pointer");
+  if (mode != 0 && mode != 1) return fail(c, MIPWA_EINVAL, "mode must be 0 or 1");
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  if (!c->norm.set || c->norm.n < 1) return fail(c, MIPWA_ESTATE, "set_norm_sample first");
+  const int T = c->tq.n, P = c->n_params, R = c->model.n_res, N = c->model.kn.n;
+  if (T < 1) return fail(c, MIPWA_ESTATE, "set_toys must come first");
+  if (c->mode != MIPWA_F32 || c->norm.dtype != MIPWA_F32 || c->model.reim || c->norm.weighted ||
+      !c->basis_on || c->gram_on)
+    return fail(c, MIPWA_ESTATE, "the tensor-core integrals need FP32 mode, float32 events, the "
+                                 "magnitude/phase form, an unweighted sample and the basis cache");
+  if (N > tc_max_knots()) return fail(c, MIPWA_EINVAL, "at most %d knots", tc_max_knots());
+  for (size_t k = 0; k < (size_t)T * P; ++k)
+    if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %zu is not finite", k);
+  const int64_t n = c->norm.n;
+  const int ev_tile = tc_events_per_tile(), per_group = tc_toys_per_group();
+  const int64_t n_tiles = (n + ev_tile - 1) / ev_tile;
+  if (n_tiles > 0x7fffffff) return fail(c, MIPWA_EINVAL, "too many events");
+  const int groups = (T + per_group - 1) / per_group;
+  const int grid = c->sm_count;
+  rc = build_basis(c, c->norm);
+  if (rc) return rc;
+  // cached basis tiles of the normalisation sample for the current knots
+  if (c->tc_norm_gen != c->norm.gen || c->tc_model_gen != c->model_gen) {
+    rc = ensure(c, (void**)&c->d_tc_tiles, &c->tc_tiles_cap, (size_t)n_tiles * tc_tile_bytes());
+    if (rc) return rc;
+    // dM_m/dy_k: the natural spline's second derivatives for each unit vector
+    const std::vector<double>& lu = c->lu_host;
+    const int nseg = N - 1, mm = N - 2;
+    const double* ih = lu.data() + nseg;
+    const double* w = ih + nseg;
+    const double* idia = w + (mm > 0 ? mm : 0);
+    const double* sup = idia + (mm > 0 ? mm : 0);
+    std::vector<double> dmdy((size_t)N * N, 0.0), y(N), v(N);
+    for (int k = 0; k < N; ++k) {
+      for (int i = 0; i < N; ++i) y[i] = i == k ? 1.0 : 0.0;
+      if (mm >= 1) {
+        for (int i = 1; i <= mm; ++i)
+          v[i - 1] = (y[i + 1] - y[i]) * ih[i] - (y[i] - y[i - 1]) * ih[i - 1];
+        for (int i = 1; i < mm; ++i) v[i] -= w[i] * v[i - 1];
+        v[mm - 1] *= idia[mm - 1];
+        for (int i = mm - 2; i >= 0; --i) v[i] = (v[i] - sup[i] * v[i + 1]) * idia[i];
+        for (int i = 1; i <= mm; ++i) dmdy[(size_t)k * N + i] = v[i - 1];
+      }
+    }
+    if (!c->d_tc_dmdy) CK(c, cudaMalloc(&c->d_tc_dmdy, (size_t)kMaxKnots * kMaxKnots * sizeof(double)));
+    CK(c, cudaMemcpyAsync(c->d_tc_dmdy, dmdy.data(), dmdy.size() * sizeof(double),
+                          cudaMemcpyHostToDevice, c->stream));
+    CK(c, launch_tc_basis(c->model.kn, c->d_tc_dmdy, (const float2*)c->norm.cur, n, c->d_tc_tiles,
+                          c->stream));
+    c->launches++;
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->tc_norm_gen = c->norm.gen;
+    c->tc_model_gen = c->model_gen;
+  }
+  // knot values of every toy group as bf16 parts in the operand layout, and
+  // the coefficients c'_r = c_r cscale_r as float pairs
+  const int tb = tc_theta_bytes(), mat = tb / 6;
+  std::vector<uint8_t> theta((size_t)groups * tb, 0);
+  std::vector<float> cr((size_t)T * 4 * kMaxRes, 0.0f);
+  for (int t = 0; t < T; ++t) {
+    const double* p = params + (size_t)t * P;
+    const int g = t / per_group, row = t % per_group;
+    for (int which = 0; which < 2; ++which)
+      for (int k = 0; k < N; ++k) {
+        const double x = p[2 * R + which * N + k];
+        const uint16_t b0 = bf16_bits((float)x);
+        const double r1 = x - bf16_value(b0);
+        const uint16_t b1 = bf16_bits((float)r1);
+        const double r2 = r1 - bf16_value(b1);
+        const uint16_t b2 = bf16_bits((float)r2);
+        const uint16_t parts[3] = {b0, b1, b2};
+        for (int q = 0; q < 3; ++q)
+          std::memcpy(&theta[(size_t)g * tb + (3 * which + q) * mat + tc_theta_offset(row, k)],
+                      &parts[q], 2);
+      }
+    for (int r = 0; r < R; ++r) {
+      const double re = p[2 * r] * c->model.cscale[r], im = p[2 * r + 1] * c->model.cscale[r];
+      float* o = &cr[(size_t)t * 4 * kMaxRes + 4 * r];
+      o[0] = (float)re;
+      o[1] = (float)(re - (double)o[0]);
+      o[2] = (float)im;
+      o[3] = (float)(im - (double)o[2]);
+    }
+  }
+  rc = ensure(c, (void**)&c->d_tc_theta, &c->tc_theta_cap, theta.size());
+  if (!rc) rc = ensure(c, (void**)&c->d_tc_cr, &c->tc_cr_cap, cr.size() * sizeof(float));
+  if (!rc) rc = ensure(c, (void**)&c->d_tc_partial, &c->tc_partial_cap,
+                       (size_t)grid * groups * per_group * sizeof(double));
+  if (rc) return rc;
+  if (!c->d_tc_dump) CK(c, cudaMalloc(&c->d_tc_dump, (size_t)4 * per_group * ev_tile * sizeof(float)));
+  CK(c, cudaMemcpyAsync(c->d_tc_theta, theta.data(), theta.size(), cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaMemcpyAsync(c->d_tc_cr, cr.data(), cr.size() * sizeof(float), cudaMemcpyHostToDevice,
+                        c->stream));
+  CK(c, cudaMemsetAsync(c->d_tc_partial, 0, (size_t)grid * groups * per_group * sizeof(double),
+                        c->stream));
+  CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->stream));
+  TcArgs a;
+  a.wtiles = c->d_tc_tiles;
+  a.basis = (const float2*)c->norm.basis;
+  a.n = n;
+  a.n_tiles = (int)n_tiles;
+  a.n_res = R;
+  a.theta = c->d_tc_theta;
+  a.cr = c->d_tc_cr;
+  a.n_toys = T;
+  a.n_groups = groups;
+  a.partial = c->d_tc_partial;
+  a.dump = c->d_tc_dump;
+  a.flags = c->d_flags;
+  CK(c, cudaEventRecord(c->ev0, c->stream));
+  CK(c, launch_tc_norm(a, grid, mode, c->stream));
+  CK(c, cudaEventRecord(c->ev1, c->stream));
+  c->launches++;
+  std::vector<double> part((size_t)grid * groups * per_group);
+  std::vector<float> dump(mode == 1 ? (size_t)4 * per_group * ev_tile : 0);
+  int flags = 0;
+  CK(c, cudaMemcpyAsync(part.data(), c->d_tc_partial, part.size() * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream));
+  if (mode == 1)
+    CK(c, cudaMemcpyAsync(dump.data(), c->d_tc_dump, dump.size() * sizeof(float),
+                          cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (flags & kFlagTcTimeout)
+    return fail(c, MIPWA_ETIMEOUT, "a tensor-core completion wait gave up");
+  if (ms) {
+    float t = 0.0f;
+    CK(c, cudaEventElapsedTime(&t, c->ev0, c->ev1));
+    *ms = t;
+  }
+  if (mode == 0) {
+    for (int t = 0; t < T; ++t) {
+      double sum = 0.0;
+      for (int b = 0; b < grid; ++b) sum += part[(size_t)b * groups * per_group + t];
+      out[t] = sum / (double)n;
+    }
+  } else {
+    for (size_t i = 0; i < dump.size(); ++i) out[i] = dump[i];
+  }
   return MIPWA_OK;
 }
 
@@ -1272,6 +1463,7 @@ int mipwa_create(mipwa_ctx** out, int device, int compute_mode) {
       cudaMalloc(&c->d_coef, coef_size(kMaxKnots, kMaxRes) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_coef32, coef32_size(kMaxKnots, kMaxRes) * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&c->d_out, kOutMax * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_rows2, 2 * kRowMax * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_flags, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->d_counter, sizeof(unsigned int)) != cudaSuccess ||
       cudaMalloc(&c->d_count, 2 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -1301,13 +1493,15 @@ void mipwa_destroy(mipwa_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   for (void* p : {(void*)c->d_lu, (void*)c->d_params, (void*)c->d_coef, (void*)c->d_coef32,
-                  (void*)c->d_out,
+                  (void*)c->d_out, (void*)c->d_rows2,
                   (void*)c->d_flags, (void*)c->d_counter, (void*)c->d_count,
                   (void*)c->d_partials, (void*)c->d_sortwork, c->data.basis, c->norm.basis,
                   (void*)c->d_cells, (void*)c->d_gram,
                   c->data.cur, c->data.spare, c->norm.cur,
                   c->norm.spare, c->norm.w_cur, c->norm.w_spare, (void*)c->d_wsum,
-                  c->d_stream_tmp})
+                  c->d_stream_tmp, (void*)c->d_tc_tiles, (void*)c->d_tc_dmdy,
+                  (void*)c->d_tc_theta, (void*)c->d_tc_cr, (void*)c->d_tc_partial,
+                  (void*)c->d_tc_dump})
     if (p) cudaFree(p);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   invalidate_graph(c);
@@ -1408,6 +1602,7 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   c->r_res = r_res;
   c->r_D = r_D;
   c->n_params = 2 * n_res + 2 * n_knots;
+  c->model_gen++;
   c->have_model = true;
   c->tq.planned = false;
   c->gram_valid = false;
@@ -1510,6 +1705,10 @@ int mipwa_nll_grad_streamed(mipwa_ctx* c, const double* params, const void* data
                             int64_t n_data, const void* norm, int64_t n_norm, int dtype,
                             double* nll, double* grad, int64_t* n_outside) {
   return run_streamed(c, params, data, n_data, norm, n_norm, dtype, nll, grad, n_outside);
+}
+
+int mipwa_toys_norm_tc(mipwa_ctx* c, const double* params, int mode, double* out, double* ms) {
+  return run_toys_norm_tc(c, params, mode, out, ms);
 }
 
 int mipwa_set_toys(mipwa_ctx* c, const void* ptr, int64_t n_total, int dtype, int on_device,

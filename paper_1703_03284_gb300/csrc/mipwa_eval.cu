@@ -74,6 +74,50 @@ __global__ void __launch_bounds__(kThreads, (kEvalMinBlocks<T, GRAD, CACHED>))
   if (threadIdx.x == 0) *a.counter = 0u;
 }
 
+// Column sums of the data rows [0, rows_d) and the normalisation rows
+// [rows_d, rows_d + rows_n) of a W-wide row array into out[0..W) and
+// out[W..2W), in a fixed order: block (x, y) takes 32 columns of sample y;
+// thread (c, l) = (tid % 32, tid / 32) sums rows l, l + 8, ... of column c,
+// then the eight lane sums are added in lane order. Many blocks, so the rows
+// stream in at memory speed rather than one block's latency.
+__global__ void __launch_bounds__(kThreads) reduce_rows_kernel(const double* partials, int W,
+                                                               int rows_d, int rows_n,
+                                                               double* out) {
+  __shared__ double lane_sum[8][33];
+  const int c = threadIdx.x & 31, l = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + c;
+  const int r0 = blockIdx.y == 0 ? 0 : rows_d, n = blockIdx.y == 0 ? rows_d : rows_n;
+  double acc = 0.0;
+  if (col < W) {
+    int r = l;
+    for (; r + 24 < n; r += 32) {
+      const double v0 = __ldcg(&partials[(size_t)(r0 + r) * W + col]);
+      const double v1 = __ldcg(&partials[(size_t)(r0 + r + 8) * W + col]);
+      const double v2 = __ldcg(&partials[(size_t)(r0 + r + 16) * W + col]);
+      const double v3 = __ldcg(&partials[(size_t)(r0 + r + 24) * W + col]);
+      acc += v0;
+      acc += v1;
+      acc += v2;
+      acc += v3;
+    }
+    for (; r < n; r += 8) acc += __ldcg(&partials[(size_t)(r0 + r) * W + col]);
+  }
+  lane_sum[l][c] = acc;
+  __syncthreads();
+  if (l == 0 && col < W) {
+    double v = 0.0;
+    for (int k = 0; k < 8; ++k) v += lane_sum[k][c];
+    out[(size_t)blockIdx.y * W + col] = v;
+  }
+}
+
+cudaError_t launch_reduce_rows(const double* partials, int W, int rows_d, int rows_n, double* out,
+                               cudaStream_t st) {
+  const dim3 grid((W + 31) / 32, 2);
+  reduce_rows_kernel<<<grid, kThreads, 0, st>>>(partials, W, rows_d, rows_n, out);
+  return cudaGetLastError();
+}
+
 // The combine step alone, for rows written by launches without finalize.
 template <typename T, bool GRAD>
 __global__ void __launch_bounds__(kThreads) finalize_kernel(const EvalArgs a, int rows_d,

@@ -39,7 +39,7 @@ struct EvalArgs {
   int finalize = 1;
 };
 
-enum { kFlagData = 1, kFlagNorm = 2, kFlagIntegral = 4 };
+enum { kFlagData = 1, kFlagNorm = 2, kFlagIntegral = 4, kFlagTcTimeout = 8 };
 
 // One unit of work of the batched-toys launch.
 struct ToyItem {
@@ -74,6 +74,31 @@ struct ToyArgs {
   double norm_count = 0.0;
 };
 
+// Tensor-core normalisation integrals of many toys (forward only).
+struct TcArgs {
+  const uint8_t* wtiles;  // cached bf16 parts of the cardinal spline basis, tile by tile
+  const float2* basis;    // cached B_r / cscale_r of the normalisation events ([r][n])
+  int64_t n;              // normalisation events
+  int n_tiles;            // ceil(n / 64)
+  int n_res;
+  const uint4* theta;     // per toy group: bf16 parts of (a_k, phi_k) in the operand layout
+  const float* cr;        // per toy, per resonance: Re c'_r hi, lo, Im c'_r hi, lo
+  int n_toys, n_groups;
+  double* partial;        // [gridDim.x][n_groups * 128]: per-block sums of |A|^2 per toy
+  float* dump;            // mode 1: products of the first tile of the first group
+  int* flags;             // kFlagTcTimeout when an mbarrier wait gave up
+};
+int tc_tile_bytes();
+int tc_theta_bytes();
+int tc_events_per_tile();
+int tc_toys_per_group();
+int tc_max_knots();
+int tc_theta_offset(int row, int k);  // byte offset of (row, k) in one operand matrix
+// the cached basis tiles of n float32 events (dmdy: N x N, dM_m/dy_k at [k N + m])
+cudaError_t launch_tc_basis(const Knots& kn, const double* dmdy, const float2* ev, int64_t n,
+                            uint8_t* tiles, cudaStream_t stream);
+cudaError_t launch_tc_norm(const TcArgs& a, int grid, int mode, cudaStream_t stream);
+
 // Spline setup for n_sets parameter vectors (params[s*P ...]) into
 // coef + s*coef_size and coef32 + s*coef32_size.
 void launch_prepare(const Model& m, const double* params, const double* lu, double* coef,
@@ -89,6 +114,10 @@ int toys_blocks_per_sm(int compute_f32, int ev_f32, bool cached, bool weighted, 
                        int block);
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t stream);
+// Column sums of rows_d data rows and rows_n normalisation rows (W wide) into
+// out: 2 rows of W doubles (data, then normalisation), in a fixed order.
+cudaError_t launch_reduce_rows(const double* partials, int W, int rows_d, int rows_n, double* out,
+                               cudaStream_t stream);
 // -2 ln L (and its gradient) from rows_d data rows at a.partials followed by
 // rows_n normalisation rows, with a.n_data data events and a.norm_count (0:
 // a.n_norm) normalisation weight; one block.
