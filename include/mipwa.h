@@ -380,7 +380,7 @@ int mipwa_kernel_time(mipwa_ctx* ctx, double* ms, int64_t* n_launches);
  * every normalisation point has weight 1 (no weighted samples here).
  *
  * It calls no allocator: every intermediate buffer lives in one fixed
- * file-scope device array of about 2.5 MB (at most 608 blocks, N <= 64 knots,
+ * file-scope device array of about 5 MB (at most 1216 blocks, N <= 64 knots,
  * R <= 4 resonances), which every GPU that loads the library holds until the
  * process exits. The first call on a device looks up that array's address;
  * make it before any CUDA stream capture. All calls share the array, so calls

@@ -436,7 +436,9 @@ __device__ __forceinline__ double sum_rows(const double* partials, int W, int co
 #pragma unroll
     for (int l = 0; l < kLanes; ++l) acc[l] += v[l];
   }
-  for (int l = 0; r < n; ++r, ++l) acc[l] += __ldcg(&partials[(size_t)(r0 + r) * W + col]);
+#pragma unroll
+  for (int l = 0; l < kLanes; ++l)
+    if (r + l < n) acc[l] += __ldcg(&partials[(size_t)(r0 + r + l) * W + col]);
   double s = 0.0;
 #pragma unroll
   for (int l = 0; l < kLanes; ++l) s += acc[l];

@@ -612,8 +612,8 @@ int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool
   const int per_sm = eval_blocks_per_sm(f32, ev32, c->model, c->basis_on,
                                         c->norm.weighted && !gram);
   int total = c->sm_count * per_sm;
-  const int64_t need_d = (c->data.n + kThreads - 1) / kThreads;
-  const int64_t need_n = (c->norm.n + kThreads - 1) / kThreads;
+  const int64_t need_d = (c->data.n + kEvalThreads - 1) / kEvalThreads;
+  const int64_t need_n = (c->norm.n + kEvalThreads - 1) / kEvalThreads;
   int nb_d = 0, nb_n = 0, grid = 0, rows = 0;
   if (gram) {
     // the event kernel runs over the data only; N-1 moment rows stand in for
@@ -732,8 +732,8 @@ int evaluate_bw(mipwa_ctx* c, const double* params, double* nll, double* grad,
     if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %d is not finite", k);
   const int ev32 = c->norm.dtype == MIPWA_F32;
   const int total = c->sm_count * eval_bw_blocks_per_sm(ev32);
-  const int64_t need_d = (c->data.n + kThreads - 1) / kThreads;
-  const int64_t need_n = (c->norm.n + kThreads - 1) / kThreads;
+  const int64_t need_d = (c->data.n + kEvalThreads - 1) / kEvalThreads;
+  const int64_t need_n = (c->norm.n + kEvalThreads - 1) / kEvalThreads;
   int nb_d = 0;
   if (c->data.n > 0) {
     const double frac = (double)c->data.n / (double)(c->data.n + c->norm.n);
@@ -997,7 +997,7 @@ int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n
     for (int p = 0; p <= pieces[s]; ++p) bounds[s][p] = sort_piece_begin(nev[s], p, pieces[s]);
     for (int p = 0; p < pieces[s]; ++p) {
       const int64_t np = bounds[s][p + 1] - bounds[s][p];
-      rows_cap += (size_t)std::min<int64_t>(total, (np + kThreads - 1) / kThreads);
+      rows_cap += (size_t)std::min<int64_t>(total, (np + kEvalThreads - 1) / kEvalThreads);
     }
   }
   for (int s = 0; s < 2; ++s) {
@@ -1070,7 +1070,7 @@ int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n
                                c->stream));
         c->launches += kSortLaunches - 1;
       }
-      const int nb = (int)std::min<int64_t>(total, (np + kThreads - 1) / kThreads);
+      const int nb = (int)std::min<int64_t>(total, (np + kEvalThreads - 1) / kEvalThreads);
       a.data = s == 0 ? piece : nullptr;
       a.norm = s == 1 ? piece : nullptr;
       a.n_data = s == 0 ? np : 0;

@@ -18,15 +18,19 @@
 
 namespace mipwa {
 
-// Resident 256-thread blocks per SM the FP32 kernels are compiled for: three
-// (up to 85 registers) for the NLL + gradient with computed Breit-Wigner
-// terms, four (64 registers) otherwise. Measured on the 40-knot workload: the
-// gradient kernels 1.2 % (magnitude/phase) and 3 % (Re/Im) faster with three,
-// the cached-basis one 12 % slower. The NLL-only kernel keeps four but runs on
-// the gradient kernel's grid (the same partition of the events, so the two
-// sum identically), 1.7 % slower than on its own.
+// Resident threads per SM the FP32 kernels are compiled for, in blocks of
+// kEvalThreads: 768 (up to 85 registers) for the NLL + gradient with computed
+// Breit-Wigner terms, 1024 (64 registers) otherwise. Measured on the 40-knot
+// workload: the gradient kernels 1.2 % (magnitude/phase) and 3 % (Re/Im)
+// faster with 768 than 1024, the cached-basis one 12 % slower. Blocks of 128
+// threads: 1.9 % faster than 256 at the same 24 warps per SM (a block's
+// periodic barrier holds fewer warps); 7 blocks 1.3 %, 8 blocks (64
+// registers) 0.7 % slower than that. The NLL-only kernel runs on the gradient
+// kernel's grid (the same partition of the events, so the two sum
+// identically), 1.7 % slower than on its own.
 template <typename T, bool GRAD, bool CACHED>
-constexpr int kEvalMinBlocks = sizeof(T) == 4 ? (GRAD && !CACHED ? 3 : 4) : 1;
+constexpr int kEvalMinBlocks =
+    sizeof(T) == 4 ? (GRAD && !CACHED ? 768 : 1024) / kEvalThreads : 1;
 
 // Events per thread per loop iteration of the FP32 NLL + gradient kernels
 // with computed Breit-Wigner terms (accumulate_range's U).
@@ -37,7 +41,7 @@ constexpr int kEvalU = sizeof(T) == 4 && GRAD && !CACHED && !BWG ? kEvalUnroll :
 // WN: the normalisation events carry weights (a.norm_w).
 template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false,
           bool WN = false>
-__global__ void __launch_bounds__(kThreads, (kEvalMinBlocks<T, GRAD, CACHED>))
+__global__ void __launch_bounds__(kEvalThreads, (kEvalMinBlocks<T, GRAD, CACHED>))
     eval_kernel(const EvalArgs a) {
   __shared__ EvalSmem<T> sm;
   const Model& m = a.model;
@@ -52,11 +56,11 @@ __global__ void __launch_bounds__(kThreads, (kEvalMinBlocks<T, GRAD, CACHED>))
   const int W = partial_width(m.kn.n, m.n_res, GRAD) + (BWG ? 2 * m.n_res : 0);
   // each block takes one contiguous chunk (a multiple of the block size), so
   // that a thread's consecutive events lie in one spline cell
-  const int64_t chunk = ((n + nb - 1) / nb + kThreads - 1) / kThreads * kThreads;
+  const int64_t chunk = ((n + nb - 1) / nb + kEvalThreads - 1) / kEvalThreads * kEvalThreads;
   const int64_t c0 = (int64_t)b * chunk;
   const int64_t c1 = c0 + chunk < n ? c0 + chunk : n;
   accumulate_range<T, EvT, GRAD, SIG, CACHED, BWG, WN, kEvalU<T, GRAD, CACHED, BWG>>(
-      sm, m, ev, cached, n, c0, c1, (int64_t)kThreads, is_data,
+      sm, m, ev, cached, n, c0, c1, (int64_t)kEvalThreads, is_data,
       a.partials + (size_t)(a.row0 + (int)blockIdx.x) * W, a.flags, a.coef, a.norm_w);
   if (!a.finalize) return;
   __threadfence();
@@ -199,7 +203,7 @@ __global__ void inside_kernel(const Model m, const EvT* ev, int64_t n, uint8_t* 
 // ------------------------------------------------------------------ launchers
 template <typename T, typename EvT, bool GRAD, int SIG = 0, bool CACHED = false, bool WN = false>
 static cudaError_t run_eval(const EvalArgs& a, int grid, cudaStream_t st) {
-  eval_kernel<T, EvT, GRAD, SIG, CACHED, false, WN><<<grid, kThreads, 0, st>>>(a);
+  eval_kernel<T, EvT, GRAD, SIG, CACHED, false, WN><<<grid, kEvalThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -244,11 +248,11 @@ cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& 
 
 cudaError_t launch_eval_bw(int ev_f32, const EvalArgs& a, int grid, cudaStream_t st) {
   if (a.norm_w) {
-    if (ev_f32) eval_kernel<double, float2, true, 0, false, true, true><<<grid, kThreads, 0, st>>>(a);
-    else eval_kernel<double, double2, true, 0, false, true, true><<<grid, kThreads, 0, st>>>(a);
+    if (ev_f32) eval_kernel<double, float2, true, 0, false, true, true><<<grid, kEvalThreads, 0, st>>>(a);
+    else eval_kernel<double, double2, true, 0, false, true, true><<<grid, kEvalThreads, 0, st>>>(a);
   } else {
-    if (ev_f32) eval_kernel<double, float2, true, 0, false, true><<<grid, kThreads, 0, st>>>(a);
-    else eval_kernel<double, double2, true, 0, false, true><<<grid, kThreads, 0, st>>>(a);
+    if (ev_f32) eval_kernel<double, float2, true, 0, false, true><<<grid, kEvalThreads, 0, st>>>(a);
+    else eval_kernel<double, double2, true, 0, false, true><<<grid, kEvalThreads, 0, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -257,10 +261,10 @@ int eval_bw_blocks_per_sm(int ev_f32) {
   int nb = 0;
   if (ev_f32)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &nb, eval_kernel<double, float2, true, 0, false, true>, kThreads, 0);
+        &nb, eval_kernel<double, float2, true, 0, false, true>, kEvalThreads, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &nb, eval_kernel<double, double2, true, 0, false, true>, kThreads, 0);
+        &nb, eval_kernel<double, double2, true, 0, false, true>, kEvalThreads, 0);
   return nb > 0 ? nb : 1;
 }
 
@@ -286,7 +290,7 @@ template <typename T, typename EvT, bool GRAD, int SIG = 0, bool CACHED = false>
 static int occ() {
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<T, EvT, GRAD, SIG, CACHED>,
-                                                kThreads, 0);
+                                                kEvalThreads, 0);
   return nb > 0 ? nb : 1;
 }
 

@@ -10,6 +10,7 @@
 namespace mipwa {
 
 constexpr int kThreads = 256;        // threads per block of the event kernels
+constexpr int kEvalThreads = 128;    // threads per block of eval_kernel (one row per block)
 constexpr int kMaxBlock = 512;       // largest block of the batched-toys kernel
 constexpr int kFlushIters = 64;      // FP32 form: grid-stride iterations between bin flushes
 

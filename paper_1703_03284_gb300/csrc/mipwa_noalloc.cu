@@ -25,7 +25,7 @@ namespace {
 
 // Largest grid the allocation-free path launches; each block needs one row
 // of per-block partial sums.
-constexpr int kRows = 608;
+constexpr int kRows = 1216;
 constexpr int kWidth = 1 + 2 * kMaxRes + 8 * kMaxSeg;  // widest partial row
 constexpr int kLU = 2 * kMaxSeg + 3 * (kMaxKnots - 2);
 constexpr int kParams = 2 * kMaxRes + 2 * kMaxKnots;
@@ -43,7 +43,7 @@ constexpr size_t kOffOutside = kOffFlags + 1;                 // unsigned long l
 constexpr size_t kOffPartials = (kOffOutside + 1 + 31) / 32 * 32;
 constexpr size_t kScratchDoubles = kOffPartials + (size_t)kRows * kWidth;
 
-// The scratch: about 2.5 MB, held by every GPU that loads the library until
+// The scratch: about 5 MB, held by every GPU that loads the library until
 // the process exits. Shared by all calls; it keeps the last call's contents.
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
@@ -127,15 +127,16 @@ extern "C" int mipwa_nll_grad_noalloc(int device, int compute_mode, double mD, d
   factor_spline_into(m.kn, lu);
 
   // ---- grid: as the context API (SMs x resident blocks), capped at the
-  // scratch rows (608 = 152 SMs x 4 blocks: the whole grid on GB300)
+  // scratch rows (1216 = 152 SMs x 8 blocks of 128 threads: the whole grid
+  // on GB300)
   int sm_count = 0;
   CKN(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
   const int f32 = compute_mode == MIPWA_F32, ev32 = dtype == MIPWA_F32;
   int total = sm_count * eval_blocks_per_sm(f32, ev32, m, false);
   if (total > kRows) total = kRows;
   if (total < 2) total = 2;
-  const int64_t need_d = (n_data + kThreads - 1) / kThreads;
-  const int64_t need_n = (n_norm + kThreads - 1) / kThreads;
+  const int64_t need_d = (n_data + kEvalThreads - 1) / kEvalThreads;
+  const int64_t need_n = (n_norm + kEvalThreads - 1) / kEvalThreads;
   int nb_d = 0;
   if (n_data > 0) {
     nb_d = (int)std::lround(total * ((double)n_data / (double)(n_data + n_norm)));
