@@ -67,7 +67,8 @@ struct SmemCommon {
   double bind[kMaxSeg * 8];   // FP64 bins of the polynomial adjoints
   double red[kMaxBlock / 32][1 + 4 * kMaxRes];
   double fin_d[1 + 4 * kMaxRes + 8 * kMaxSeg];
-  double fin_n[1 + 4 * kMaxRes + 8 * kMaxSeg];
+  double fin_n[1 + 4 * kMaxRes + 8 * kMaxSeg];  // later also the staged spline system
+  static_assert(1 + 4 * kMaxRes + 8 * kMaxSeg >= 5 * kMaxKnots, "room for SplineLU");
   double ybar[2][kMaxKnots];
   double mbar[2][kMaxKnots];
   int is_last;
@@ -473,48 +474,65 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
     for (int col = 1 + threadIdx.x; col < W; col += blockDim.x)
       sm.fin_d[col] = -2.0 * sm.fin_d[col] + kappa * sm.fin_n[col];
     __syncthreads();
+    // the factored spline system, staged where fin_n was (read serially below)
+    double* lus = sm.fin_n;
+    for (int i = threadIdx.x; i < SplineLU::size(N); i += blockDim.x) lus[i] = lu[i];
+    __syncthreads();
     for (int k = threadIdx.x; k < 2 * R; k += blockDim.x) {
       // FP32 form: the kernel accumulated against A_r / cscale_r
       const double sc = std::is_same<T, float>::value ? m.cscale[k >> 1] : 1.0;
       out[1 + k] = sm.fin_d[1 + k] * sc;
       if constexpr (BWG) out[1 + 2 * R + 2 * N + k] = sm.fin_d[W0 + k];
     }
-    // one thread per spline, in different warps
-    const int sp = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 ? 1 : -1);
-    if (sp >= 0) {
-      const double* h = lu;
-      const double* ih = lu + nseg;
-      const double* w = lu + 2 * nseg;
-      const double* idia = w + (N - 2);
-      const double* sup = idia + (N - 2);
-      double* yb = sm.ybar[sp];
-      double* mb = sm.mbar[sp];
-      for (int k = 0; k < N; ++k) yb[k] = mb[k] = 0.0;
-      const double* G = &sm.fin_d[1 + 2 * R];
-      for (int j = 0; j < nseg; ++j) {
-        const double g0 = G[j * 8 + sp * 4 + 0], g1 = G[j * 8 + sp * 4 + 1];
-        const double g2 = G[j * 8 + sp * 4 + 2], g3 = G[j * 8 + sp * 4 + 3];
-        yb[j] += g0 - g1 * ih[j];
-        yb[j + 1] += g1 * ih[j];
-        mb[j] += -g1 * h[j] / 3.0 + 0.5 * g2 - g3 * ih[j] / 6.0;
-        mb[j + 1] += -g1 * h[j] / 6.0 + g3 * ih[j] / 6.0;
+    // the spline adjoint of each spline (sp = 0: magnitude or real part,
+    // 1: phase or imaginary part): bins -> (ybar, Mbar) per knot, in parallel
+    // (each sum in the order of a pass over the segments), the transposed
+    // solve Mbar -> T^{-1} Mbar serially, then D^T per knot in parallel
+    const double* h = lus;
+    const double* ih = lus + nseg;
+    const double* w = lus + 2 * nseg;
+    const double* idia = w + (N - 2);
+    const double* sup = idia + (N - 2);
+    const double* G = &sm.fin_d[1 + 2 * R];
+    constexpr double third = 1.0 / 3.0, sixth = 1.0 / 6.0;  // products: FP64 divisions are slow
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+      const int sp = t / N, k = t % N;
+      double y = 0.0, mv = 0.0;
+      if (k >= 1) {  // segment k-1's right end
+        const double* g = &G[(k - 1) * 8 + sp * 4];
+        y += g[1] * ih[k - 1];
+        mv += -g[1] * h[k - 1] * sixth + g[3] * ih[k - 1] * sixth;
       }
-      const int mm = N - 2;
-      if (mm >= 1) {
-        // v = T^{-1} Mbar_interior (T is symmetric), reusing mb[1..N-2] in place
-        double* v = mb + 1;
-        for (int i = 1; i < mm; ++i) v[i] -= w[i] * v[i - 1];
-        v[mm - 1] *= idia[mm - 1];
-        for (int i = mm - 2; i >= 0; --i) v[i] = (v[i] - sup[i] * v[i + 1]) * idia[i];
-        // (D y)_k = (y_{k+1} - y_k)/h_k - (y_k - y_{k-1})/h_{k-1}, k = 1..N-2
-        for (int k = 1; k <= N - 2; ++k) {
-          const double vk = v[k - 1];
-          yb[k + 1] += vk * ih[k];
-          yb[k] -= vk * (ih[k] + ih[k - 1]);
-          yb[k - 1] += vk * ih[k - 1];
-        }
+      if (k < nseg) {  // segment k's left end
+        const double* g = &G[k * 8 + sp * 4];
+        y += g[0] - g[1] * ih[k];
+        mv += -g[1] * h[k] * third + 0.5 * g[2] - g[3] * ih[k] * sixth;
       }
-      for (int k = 0; k < N; ++k) out[1 + 2 * R + sp * N + k] = yb[k];
+      sm.ybar[sp][k] = y;
+      sm.mbar[sp][k] = mv;
+    }
+    __syncthreads();
+    const int mm = N - 2;
+    // one thread per spline, in different warps: v = T^{-1} Mbar_interior (T
+    // is symmetric), in place in mbar[sp][1..N-2]
+    const int sp1 = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 ? 1 : -1);
+    if (sp1 >= 0 && mm >= 1) {
+      double* v = sm.mbar[sp1] + 1;
+      for (int i = 1; i < mm; ++i) v[i] -= w[i] * v[i - 1];
+      v[mm - 1] *= idia[mm - 1];
+      for (int i = mm - 2; i >= 0; --i) v[i] = (v[i] - sup[i] * v[i + 1]) * idia[i];
+    }
+    __syncthreads();
+    // ybar += D^T v, (D y)_k = (y_{k+1} - y_k)/h_k - (y_k - y_{k-1})/h_{k-1},
+    // k = 1..N-2: knot p takes the terms of k = p-1, p, p+1 in that order
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+      const int sp = t / N, p = t % N;
+      const double* v = sm.mbar[sp];  // v_k at v[k], k = 1..N-2
+      double y = sm.ybar[sp][p];
+      if (p - 1 >= 1 && p - 1 <= mm) y += v[p - 1] * ih[p - 1];
+      if (p >= 1 && p <= mm) y -= v[p] * (ih[p] + ih[p - 1]);
+      if (p + 1 >= 1 && p + 1 <= mm) y += v[p + 1] * ih[p];
+      out[1 + 2 * R + sp * N + p] = y;
     }
   }
 }

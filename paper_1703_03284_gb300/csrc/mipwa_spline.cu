@@ -24,10 +24,13 @@ __global__ void prepare_kernel(const Model m, const double* __restrict__ params,
   coef += (size_t)blockIdx.x * coef_size(N, n_res);
   coef32 += (size_t)blockIdx.x * coef32_size(N, n_res);
   __shared__ double M[2][kMaxKnots];
+  __shared__ double lus[5 * kMaxKnots];  // the factored system, read serially below
   const int nseg = N - 1, mm = N - 2;
-  const double* h = lu;
-  const double* ih = lu + nseg;
-  const double* w = lu + 2 * nseg;
+  for (int i = threadIdx.x; i < SplineLU::size(N); i += blockDim.x) lus[i] = lu[i];
+  __syncthreads();
+  const double* h = lus;
+  const double* ih = lus + nseg;
+  const double* w = lus + 2 * nseg;
   const double* idia = w + mm;
   const double* sup = idia + mm;
   const double* y_all = params + 2 * n_res;
@@ -53,9 +56,10 @@ __global__ void prepare_kernel(const Model m, const double* __restrict__ params,
     const double M0 = M[s][j], M1 = M[s][j + 1];
     double a[4];
     a[0] = y[j];
-    a[1] = (y[j + 1] - y[j]) * ih[j] - h[j] * (2.0 * M0 + M1) / 6.0;
+    constexpr double sixth = 1.0 / 6.0;  // a product: divisions are slow on the FP64 pipe
+    a[1] = (y[j + 1] - y[j]) * ih[j] - h[j] * (2.0 * M0 + M1) * sixth;
     a[2] = 0.5 * M0;
-    a[3] = (M1 - M0) * ih[j] / 6.0;
+    a[3] = (M1 - M0) * ih[j] * sixth;
     double* c = coef + j * 8 + s * 4;
     for (int k = 0; k < 4; ++k) c[k] = a[k];
     // FP32 form: the same cubic about float(s_j) (exact Taylor shift by d),
