@@ -71,10 +71,13 @@ def _measured_hbm_gbs() -> float:
 
 HBM_GBS = _measured_hbm_gbs()
 # DRAM bytes (read + write) of the fused FP32 NLL+gradient kernel per event
-# processed, from one ncu capture on 2e7 + 2e7 events (320.45 MB read + 4.01
+# processed, from one ncu capture on 2e7 + 2e7 events (320.53 MB read + 4.01
 # MB written per launch); a launch's traffic is this times its events. None
 # once the kernel has changed since the capture.
-TRAFFIC_PER_EVENT = (320.449536e6 + 4.005888e6) / 4e7
+TRAFFIC_PER_EVENT = (320.530432e6 + 4.007680e6) / 4e7
+# The same for the cached-basis kernel (960.13 MB read + 3.65 MB written for
+# 2e7 + 2e7 events with their cached Breit-Wigner terms).
+TRAFFIC_PER_EVENT_CACHED = (960.130816e6 + 3.650560e6) / 4e7
 
 
 def parse():
@@ -830,7 +833,8 @@ def run(args, world, rank, local, stream):
                   "roofline": {"bound": "alu", "achieved": achc, "peak": peak32,
                                "unit": "TFLOP/s", "frac": achc / peak32,
                                "hbm_gbs": hbm, "hbm_frac_of_measured": hbm / HBM_GBS,
-                               "traffic": None,
+                               "traffic": None if TRAFFIC_PER_EVENT_CACHED is None
+                               else TRAFFIC_PER_EVENT_CACHED * events,
                                "kernel": "eval_kernel<float,float2,grad,cached>"}}
 
     # ---- Re/Im S-wave form: direct, and with the per-cell moment normalisation
