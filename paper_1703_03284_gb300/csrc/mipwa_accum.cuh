@@ -538,7 +538,8 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
 }
 
 // Accumulate the events first, first + stride, ... < end of one sample
-// (cached basis: resonance-major over the sample's n events) into one partial
+// (end - first < 2^31, as every sample holds fewer than 2^31 events; cached
+// basis: resonance-major over the sample's n events) into one partial
 // row: [sum ln|A|^2 (data) or sum |A|^2 (normalisation), c_r adjoint (2R),
 // spline polynomial adjoints (8 (N-1))]. The per-evaluation model data must be
 // staged in sm; the bins are zeroed here. Every thread of the block calls this.
@@ -572,16 +573,14 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   int iter = 0;
   // FP32 form: the spline adjoint of the thread's events is summed in
   // registers while they stay in one spline cell (events are grouped by cell
-  // and a thread's consecutive events are 256 apart); every kRegIters
-  // iterations the warp adds its sums to the shared bins (one reduce-scatter
-  // when the warp shares the cell), and a lane whose cell changes adds its own.
-  // (Measured on the 40-knot workload: 64 iterations, once per flush of the
-  // shared bins to FP64, 0.8 % faster than 16.)
+  // and a thread's consecutive events are a block apart); every kFlushIters
+  // iterations (counted by iter) the warp adds its sums to the shared bins
+  // (one reduce-scatter when the warp shares the cell), just before the
+  // shared bins go to FP64, and a lane whose cell changes adds its own.
+  // (Measured on the 40-knot workload: 64 iterations 0.8 % faster than 16.)
   constexpr bool kThreadBins = std::is_same<T, float>::value;
-  constexpr int kRegIters = kFlushIters;
   T acc[16];
   int cur = -1;
-  int reg_iter = 0;
 #pragma unroll
   for (int k = 0; k < 16; ++k) acc[k] = T(0);
   // computed basis: the next iteration's event is loaded one iteration ahead
@@ -591,8 +590,9 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   if constexpr (!CACHED && U == 1) {
     if (first + threadIdx.x < end) e_next = ev[first + threadIdx.x];
   }
-  // the per-event work: amplitude (B given when PRE), sums, adjoint
-  auto one = [&](const EvT& e, int64_t i, const Cplx<T>* Bpre) {
+  // the per-event work: amplitude (B given when PRE), sums, adjoint; live:
+  // i < end
+  auto one = [&](const EvT& e, int64_t i, bool live, const Cplx<T>* Bpre) {
     bool ok = false;
     SwaveState<T> sw;
     Cplx<T> A{T(0), T(0)};
@@ -603,7 +603,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
     }
     Cplx<double> dBm[BWG ? kMaxRes : 1], dBw[BWG ? kMaxRes : 1];
     T wt = T(1);
-    if (i < end) {
+    if (live) {
       const T s12 = (T)e.x, s13 = (T)e.y;
       if constexpr (BWG) {
         bw_basis_deriv(m, (double)s12, (double)s13, B, dBm, dBw);
@@ -682,10 +682,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
 #pragma unroll
           for (int k = 0; k < 16; ++k) acc[k] += v[k];
         }
-        if (++reg_iter == kRegIters) {
-          reg_iter = 0;
-          flush_bins_warp(sm, cur, acc);
-        }
+        if (iter + 1 == kFlushIters) flush_bins_warp(sm, cur, acc);
       } else {
         bin_swave_warp(sm, ok, ok ? sw.j12() : 0, ok ? sw.j13() : 0, v);
       }
@@ -703,15 +700,18 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
     }
   };
   if constexpr (U == 1) {
-    for (int64_t base = first; base < end; base += stride) {
-      const int64_t i = base + threadIdx.x;
+    // 32-bit offsets from first (a range holds fewer than 2^31 events)
+    const int nloc = (int)(end - first), st = (int)stride;
+    const EvT* evf = ev + first;
+    for (int b = 0; b < nloc; b += st) {
+      const int k = b + (int)threadIdx.x;
       EvT e = e_next;
       if constexpr (!CACHED) {
-        if (i + stride < end) e_next = ev[i + stride];
+        if (k < nloc - st) e_next = evf[k + st];
       } else {
-        if (i < end) e = ev[i];
+        if (k < nloc) e = evf[k];
       }
-      one(e, i, nullptr);
+      one(e, first + k, k < nloc, nullptr);
     }
   } else {
     // U events per thread per iteration; with computed Breit-Wigner terms the
@@ -731,7 +731,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
         for (int u = 0; u < U; ++u) basis_of<T, SIG>(m, (T)e[u].x, (T)e[u].y, Bp[u]);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) one(e[u], ii[u], Bp[u]);
+      for (int u = 0; u < U; ++u) one(e[u], ii[u], ii[u] < end, Bp[u]);
     }
   }
   if (bad) atomicOr(flags, is_data ? kFlagData : kFlagNorm);
