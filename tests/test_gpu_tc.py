@@ -79,3 +79,36 @@ def test_tc_integrals_match_oracle(problem):
     # the cached basis is reused, and a new sample is picked up
     I2, _ = lik.toys_norm_tc(params, mode=0)
     np.testing.assert_allclose(I2, I, rtol=1e-12)
+
+
+def test_tc_errors(problem):
+    """The entry point's refusals: a bad mode or parameter, FP64 mode, and
+    no toys yet."""
+    import ctypes
+    from paper_1703_03284_gb300 import F64, MipwaError, _lib
+    name, spec, lik, params, stored = problem
+    with pytest.raises(MipwaError, match="EINVAL"):
+        lik.toys_norm_tc(params, mode=2)
+    bad = params.copy()
+    bad[3, 0] = np.nan
+    with pytest.raises(MipwaError, match="EINVAL"):
+        lik.toys_norm_tc(bad, mode=0)
+    norm = torch.from_numpy(P.uniform_sample(name, 1000, f32=True)).to("cuda:0")
+    pool = torch.from_numpy(P.data_sample(name, 20, seed=6, f32=True)).to("cuda:0")
+    l64 = Likelihood(0, F64)
+    l64.set_spec(spec)
+    l64.set_norm_sample(norm)
+    l64.set_toys(pool, np.array([0, 10, 20], dtype=np.int64))
+    with pytest.raises(MipwaError, match="ESTATE"):
+        l64.toys_norm_tc(params[:2], mode=0)
+    # no toys set: the C entry point itself refuses
+    l32 = Likelihood(0, F32)
+    l32.set_spec(spec)
+    l32.set_norm_sample(norm)
+    p = np.ascontiguousarray(params[0])
+    out = np.zeros(1)
+    ms = ctypes.c_double(0.0)
+    pd = ctypes.POINTER(ctypes.c_double)
+    rc = l32._lib.mipwa_toys_norm_tc(l32._h, p.ctypes.data_as(pd), 0, out.ctypes.data_as(pd),
+                                     ctypes.byref(ms))
+    assert rc == _lib.ESTATE

@@ -189,3 +189,21 @@ def test_toys_equal_single_fits():
         v, g = single.nll_grad(params[t])
         assert abs(nll[t] - v) <= 1e-12 * max(abs(v), 1.0)
         np.testing.assert_allclose(grad[t], g, rtol=1e-9, atol=1e-9 * (np.abs(g).max() + 1))
+
+
+def test_toys_config_refusals():
+    """Out-of-range launch configurations are refused and leave the current
+    one in place."""
+    from paper_1703_03284_gb300 import MipwaError
+    name = "kpipi_n40"
+    spec, pool, offsets, norm, params = toy_problem(name, True)
+    lik = make_toys(name, pool, offsets, norm, F32, cached=True)
+    lik.set_toys_config(norm_chunk=131072, data_chunk=65536, block=256, blocks_per_sm=2)
+    before = lik.toys_config()
+    for bad in (dict(norm_chunk=100), dict(data_chunk=(1 << 30) + 1), dict(block=100),
+                dict(block=1024), dict(blocks_per_sm=17), dict(blocks_per_sm=-1)):
+        with pytest.raises(MipwaError, match="EINVAL"):
+            lik.set_toys_config(**bad)
+        assert lik.toys_config() == before
+    nll, grad = lik.nll_grad_toys(params)
+    check_toys(nll, grad, oracle_toys(name, True, tuple(SIZES), 40_000), SIZES, True)
