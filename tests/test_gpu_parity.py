@@ -130,6 +130,44 @@ def test_inside_matches_oracle():
         np.testing.assert_array_equal(got32, o.inside(box.astype(np.float32).astype(np.float64)))
 
 
+def _near_boundary(spec, n, seed):
+    """Points placed relative 1e-9 .. 1e-3 off the Dalitz boundary (both
+    edges of the s23 range at fixed s12, and s12 near its thresholds), in
+    both orders of (s12, s13)."""
+    rng = np.random.default_rng(seed)
+    m1, m2, mD = spec.m1, spec.m2, spec.mD
+    smin, smax = (m1 + m2) ** 2, (mD - m2) ** 2
+    t = np.concatenate([rng.uniform(smin, smax, n // 2),
+                        smin * (1 + 10 ** rng.uniform(-7, -1, n // 4)),
+                        smax * (1 - 10 ** rng.uniform(-7, -1, n - n // 2 - n // 4))])
+    e2 = (t - m1 * m1 + m2 * m2) / (2 * np.sqrt(t))
+    e3 = (mD * mD - t - m2 * m2) / (2 * np.sqrt(t))
+    k2 = np.sqrt(np.maximum(e2 * e2 - m2 * m2, 0))
+    k3 = np.sqrt(np.maximum(e3 * e3 - m2 * m2, 0))
+    es = (e2 + e3) ** 2
+    b = np.where(rng.random(n) < 0.5, es - (k2 + k3) ** 2, es - (k2 - k3) ** 2)
+    b = b * (1 + rng.choice([-1, 1], n) * 10 ** rng.uniform(-9, -3, n))
+    s13 = (mD * mD + m1 * m1 + 2 * m2 * m2) - t - b
+    pts = np.stack([np.concatenate([t, s13]), np.concatenate([s13, t])], axis=1)
+    return pts
+
+
+def test_inside_near_boundary_matches_oracle():
+    """float32 events within 1e-9 .. 1e-3 (relative) of the boundary: the FP32
+    decision with its error margin, and the FP64 test behind it, classify
+    exactly as the oracle does on the same float32 values."""
+    for name in ("pipipi_n10", "kpipi_n40", "kkk_n40"):
+        spec = P.spec_by_name(name)
+        o = P.oracle_for(name)
+        pts = _near_boundary(spec, 400_000, 5).astype(np.float32)
+        lik = Likelihood(0, F32)
+        lik.set_masses(spec.mD, spec.m1, spec.m2)
+        got = lik.inside(torch.from_numpy(pts).to(DEV)).cpu().numpy()
+        ref = o.inside(pts.astype(np.float64))
+        assert 0.2 < ref.mean() < 0.8
+        np.testing.assert_array_equal(got, ref)
+
+
 def test_set_events_rejects_outside_and_keeps_state():
     name = "pipipi_n10"
     data, norm = P.data_sample(name, 3000), P.grid_sample(name, 50)
