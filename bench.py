@@ -855,14 +855,24 @@ def run(args, world, rank, local, stream):
         torch.cuda.nvtx.range_push("e2e")
         g0.record(stream)
         step_ms = []
-        for _ in range(args.e2e_steps):
+        # per-step CUDA events on the library's stream: a slow step with a
+        # normal device span was held up on the host, a slow device span on
+        # the GPU or the host link
+        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.e2e_steps)]
+        for k in range(args.e2e_steps):
             t_a = time.perf_counter()
+            sev[k][0].record(stream)
             lik.nll_grad_streamed(params, data_h, norm_h)
+            sev[k][1].record(stream)
             step_ms.append(1e3 * (time.perf_counter() - t_a))
         g1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         te = max_over_ranks(g0.elapsed_time(g1), world)
+        dev_ms = [a.elapsed_time(b) for a, b in sev]
+        med = statistics.median(step_ms)
+        slow = [(round(h, 2), round(dv, 2)) for h, dv in zip(step_ms, dev_ms) if h > 1.5 * med]
         # the three-call path on the same buffers
         n3 = max(3, args.e2e_steps // 5)
         for _ in range(2):
@@ -908,6 +918,8 @@ def run(args, world, rank, local, stream):
                # copies stall); the mean above includes such steps
                "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
                            "max": max(step_ms)},
+               "device_step_ms": {"median": statistics.median(dev_ms), "max": max(dev_ms)},
+               "slow_steps_host_device_ms": slow,
                "three_call_path": {"ms_per_step": t3, "steps": n3,
                                    "step_ms_median": statistics.median(step3),
                                    "calls": "set_events + set_norm_sample + nll_grad"}}

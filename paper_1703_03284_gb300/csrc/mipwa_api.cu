@@ -89,7 +89,8 @@ struct mipwa_ctx {
   // overlaps the previous sample's sort on the context stream
   cudaStream_t copy_stream = nullptr;
   static constexpr int kCopyPieces = 8;  // a sorted sample arrives in pieces, each counted on arrival
-  cudaEvent_t piece_done[2 * kCopyPieces] = {};  // streamed call: data pieces, then norm pieces
+  static constexpr int kPieceEvents = 16;  // copy events per sample (kCopyPieces or more)
+  cudaEvent_t piece_done[2 * kPieceEvents] = {};  // streamed call: data pieces, then norm pieces
   void* d_stream_tmp = nullptr;  // streamed call: the sort's middle buffer for one piece at a time
   size_t stream_tmp_cap = 0;
   bool basis_on = false;
@@ -946,12 +947,15 @@ int run_toys(mipwa_ctx* c) {
   return MIPWA_OK;
 }
 
-// The streamed call takes a sample in kStreamPieces pieces, each grouped and
-// evaluated on its own, and copies each piece in kStreamSub sub-pieces
-// (halving), each counted (the sort's first pass and the Dalitz check) as it
-// lands. 2 x 4 = kCopyPieces copy events per sample.
-constexpr int kStreamPieces = 2;
+// The streamed call takes a sample in pieces, each grouped and evaluated on
+// its own, and copies each piece in kStreamSub sub-pieces (halving), each
+// counted (the sort's first pass and the Dalitz check) as it lands. The
+// pieces of each sample, in copy order, end at the fractions below (samples
+// under 2^16 events: one piece).
+constexpr int kStreamMaxPieces = 4;
 constexpr int kStreamSub = 4;
+constexpr double kStreamPlan[2][kStreamMaxPieces] = {{0.5, 1.0, 0.0, 0.0}, {0.5, 1.0, 0.0, 0.0}};
+constexpr int kStreamPlanLen[2] = {2, 2};
 
 // One pipelined call: copy both samples from host memory in pieces and, as
 // each piece lands, check it against the Dalitz plot, group it by spline
@@ -982,19 +986,21 @@ int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n
   const size_t eb = ev_bytes(dtype);
   const int total = c->sm_count * eval_blocks_per_sm(f32, ev32, c->model, false, false);
   const int W = partial_width(c->model.kn.n, c->model.n_res, true);
-  static_assert(kStreamPieces * kStreamSub == mipwa_ctx::kCopyPieces, "copy events");
+  static_assert(kStreamMaxPieces * kStreamSub <= mipwa_ctx::kPieceEvents, "copy events");
   mipwa_ctx::Sample* smp[2] = {&c->data, &c->norm};
   const void* src[2] = {data, norm};
   const int64_t nev[2] = {n_data, n_norm};
-  // pieces of a sample: two halves from 2^16 events up, one piece below
-  // (each piece costs its sort and its evaluation a fixed ~0.3 ms on GB300;
-  // two halves keep the GPU work of a step close to its copy time)
+  // pieces of a sample (each piece costs its sort and its evaluation a fixed
+  // ~0.3 ms on GB300, so a few pieces keep the GPU work of a step close to
+  // its copy time)
   int pieces[2];
-  int64_t bounds[2][mipwa_ctx::kCopyPieces + 1];
+  int64_t bounds[2][kStreamMaxPieces + 1];
   size_t rows_cap = 0;
   for (int s = 0; s < 2; ++s) {
-    pieces[s] = nev[s] >= (1 << 16) ? kStreamPieces : 1;
-    for (int p = 0; p <= pieces[s]; ++p) bounds[s][p] = sort_piece_begin(nev[s], p, pieces[s]);
+    pieces[s] = nev[s] >= (1 << 16) ? kStreamPlanLen[s] : 1;
+    bounds[s][0] = 0;
+    for (int p = 1; p <= pieces[s]; ++p)
+      bounds[s][p] = p == pieces[s] ? nev[s] : (int64_t)std::llround(kStreamPlan[s][p - 1] * nev[s]);
     for (int p = 0; p < pieces[s]; ++p) {
       const int64_t np = bounds[s][p + 1] - bounds[s][p];
       rows_cap += (size_t)std::min<int64_t>(total, (np + kEvalThreads - 1) / kEvalThreads);
@@ -1031,7 +1037,7 @@ int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n
         if (q1 > q0)
           CK(c, cudaMemcpyAsync((char*)smp[s]->spare + q0 * eb, (const char*)src[s] + q0 * eb,
                                 (q1 - q0) * eb, cudaMemcpyHostToDevice, c->copy_stream));
-        CK(c, cudaEventRecord(c->piece_done[(s * kStreamPieces + p) * kStreamSub + q],
+        CK(c, cudaEventRecord(c->piece_done[(s * kStreamMaxPieces + p) * kStreamSub + q],
                               c->copy_stream));
       }
     }
@@ -1057,7 +1063,7 @@ int run_streamed(mipwa_ctx* c, const double* params, const void* data, int64_t n
       char* piece = (char*)smp[s]->spare + e0 * eb;
       for (int q = 0; q < kStreamSub; ++q) {
         CK(c, cudaStreamWaitEvent(c->stream,
-                                  c->piece_done[(s * kStreamPieces + p) * kStreamSub + q], 0));
+                                  c->piece_done[(s * kStreamMaxPieces + p) * kStreamSub + q], 0));
         if (np > 0) {
           CK(c, launch_sort_count_checked(ev32, c->model, piece, np, c->d_sortwork,
                                           c->d_count + s, c->stream, q, kStreamSub));
