@@ -65,6 +65,12 @@ def test_streamed_fp64_matches_oracle_and_set_path():
     p2 = synth.perturbed_params(spec, 4)
     v3, g3 = lik.nll_grad_streamed(p2, d2, n2)
     check(v3, g3, *o.nll_grad(p2, d2, n2), False)
+    # either side of the two-piece threshold (2^16 events): an odd split of
+    # the data into two pieces, the normalisation sample in one
+    d3 = P.data_sample(name, 65_537, seed=9)
+    n3 = P.uniform_sample(name, 65_535, seed=10)
+    v5, g5 = lik.nll_grad_streamed(p2, d3, n3)
+    check(v5, g5, *o.nll_grad(p2, d3, n3), False)
     # no data events: only the normalisation term, its gradient zero
     v4, g4 = lik.nll_grad_streamed(p2, np.zeros((0, 2)), n2)
     assert v4 == 0.0 and np.all(g4 == 0.0)
