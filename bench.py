@@ -425,6 +425,15 @@ def toys_leg(args, stream, rank):
     t_ms = e0.elapsed_time(e1) / args.toys_steps
     launches_it = (lik.launch_count() - launches0) / args.toys_steps
     pairs = int(offsets[-1]) + args.n_toys * args.toys_norm
+    # the same evaluation without the gradient (mipwa_nll_toys)
+    lik.nll_toys(params)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.toys_steps):
+        lik.nll_toys(params)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_nll_ms = e0.elapsed_time(e1) / args.toys_steps
     # looping single-toy evaluations (a few toys timed, scaled to all toys by events)
     loop = {}
     for mode, name in ((F64, "fp64"), (F32, "fp32")):
@@ -475,6 +484,8 @@ def toys_leg(args, stream, rank):
             "norm_events": args.toys_norm, "ms_per_iteration": t_ms,
             "toys_per_s": 1e3 * args.n_toys / t_ms,
             "event_pairs_per_s": pairs / (t_ms / 1e3),
+            "nll_only": {"ms_per_iteration": t_nll_ms, "toys_per_s": 1e3 * args.n_toys / t_nll_ms,
+                         "note": "mipwa_nll_toys, same launch configuration, no gradient"},
             "autotuned": dict(best, seconds=t_tune),
             "gpu_launches_per_iteration": launches_it,
             "loop_single_toy": loop,

@@ -262,6 +262,16 @@ int mipwa_set_toys(mipwa_ctx* ctx, const void* s12s13, int64_t n_total, int dtyp
  * nll: n_toys; grad: n_toys * P. Blocks until done. */
 int mipwa_nll_grad_toys(mipwa_ctx* ctx, const double* params, double* nll, double* grad);
 
+/* -2 ln L of every toy at its own parameter vector, without the gradient
+ * (the objective above, per toy; for minimisers and scans that need values
+ * only): the same
+ * work list and launch configuration as mipwa_nll_grad_toys, with the
+ * kernels' adjoint work left out. params: n_toys * P host doubles
+ * (toy-major); nll: n_toys host doubles. Status as mipwa_nll_grad_toys.
+ * Alternating it with mipwa_nll_grad_toys re-captures the CUDA graph at each
+ * switch. Blocks until done. */
+int mipwa_nll_toys(mipwa_ctx* ctx, const double* params, double* nll);
+
 /* Launch configuration of the batched evaluation. */
 typedef struct {
   int64_t norm_chunk; /* normalisation events per work item (default 131072) */

@@ -60,6 +60,7 @@ SIGNATURES = [
     ("mipwa_nll_grad_streamed", _i, [_vp, _pd, _vp, _i64, _vp, _i64, _i, _pd, _pd, _pi64]),
     ("mipwa_set_toys", _i, [_vp, _vp, _i64, _i, _i, _pi64, _i, _pi64]),
     ("mipwa_nll_grad_toys", _i, [_vp, _pd, _pd, _pd]),
+    ("mipwa_nll_toys", _i, [_vp, _pd, _pd]),
     ("mipwa_toys_autotune", _i, [_vp, _pd, ctypes.POINTER(ToysConfig), ctypes.POINTER(_i)]),
     ("mipwa_set_toys_graph", _i, [_vp, _i]),
     ("mipwa_toys_norm_tc", _i, [_vp, _pd, _i, _pd, _pd]),

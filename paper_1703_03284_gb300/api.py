@@ -217,6 +217,18 @@ class Likelihood:
                                                   nll.ctypes.data_as(pd), g.ctypes.data_as(pd)))
         return nll, g
 
+    def nll_toys(self, params):
+        """params: (n_toys, P) -> nll (n_toys,), without the gradient."""
+        self._follow_stream()
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        if p.shape != (self.n_toys, self.n_params):
+            raise ValueError(f"expected params of shape {(self.n_toys, self.n_params)}")
+        nll = np.empty(self.n_toys)
+        pd = ctypes.POINTER(ctypes.c_double)
+        self._check(self._lib.mipwa_nll_toys(self._h, p.ctypes.data_as(pd),
+                                             nll.ctypes.data_as(pd)))
+        return nll
+
     def toys_autotune(self, params) -> dict:
         """Time the batched evaluation over its launch configurations, keep the
         fastest; returns it as a dict with "n_timed" (0: a cached choice)."""

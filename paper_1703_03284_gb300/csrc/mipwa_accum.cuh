@@ -485,16 +485,19 @@ __device__ __forceinline__ double sum_rows(const double* partials, int W, int co
 // [d0, d0 + dn), normalisation rows [n0, n0 + nn); writes out[0..P] (BWG: and
 // the derivatives with respect to the resonance masses and widths at
 // out[1 + P .. 1 + P + 2R), from 2R extra columns at the end of each row).
+// stride: the rows' spacing in doubles (0: their own width).
 template <typename T, bool GRAD, bool BWG = false>
 __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
                               const double* partials, int d0, int dn, int n0, int nn,
-                              int64_t n_data, double norm_count, double* out, int* flags) {
+                              int64_t n_data, double norm_count, double* out, int* flags,
+                              int stride = 0) {
   const int R = m.n_res, N = m.kn.n, nseg = N - 1;
   const int W0 = partial_width(N, R, GRAD);
   const int W = W0 + (BWG ? 2 * R : 0);
+  const int ld = stride > 0 ? stride : W;
   for (int col = threadIdx.x; col < W; col += blockDim.x) {
-    sm.fin_d[col] = sum_rows(partials, W, col, d0, dn);
-    sm.fin_n[col] = sum_rows(partials, W, col, n0, nn);
+    sm.fin_d[col] = sum_rows(partials, ld, col, d0, dn);
+    sm.fin_n[col] = sum_rows(partials, ld, col, n0, nn);
   }
   __syncthreads();
   const double S = sm.fin_n[0];

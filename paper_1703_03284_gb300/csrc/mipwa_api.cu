@@ -136,6 +136,7 @@ struct mipwa_ctx {
     bool planned = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool graph_grad = true;  // the captured graph evaluates the gradient too
     bool use_graph = true;
   } tq;
   int64_t launches = 0;
@@ -843,8 +844,9 @@ int plan_toys(mipwa_ctx* c) {
   return MIPWA_OK;
 }
 
-// Queue one batched evaluation (params already in q.h_params) on `st`.
-int enqueue_toys(mipwa_ctx* c, cudaStream_t st) {
+// Queue one batched evaluation (params already in q.h_params) on `st`: -2 ln L
+// of every toy, and its gradient when grad.
+int enqueue_toys(mipwa_ctx* c, cudaStream_t st, bool grad) {
   auto& q = c->tq;
   const int T = q.n, P = c->n_params;
   const int f32 = c->mode == MIPWA_F32;
@@ -882,7 +884,7 @@ int enqueue_toys(mipwa_ctx* c, cudaStream_t st) {
   a.model = c->model;
   a.norm_w = (c->norm.weighted && !c->gram_on) ? c->norm.w_cur : nullptr;
   a.norm_count = c->norm.wsum;
-  CK(c, launch_toys(f32, ev32, a, q.block, q.grid, st));
+  CK(c, launch_toys(f32, ev32, a, q.block, q.grid, st, grad));
   CK(c, cudaMemcpyAsync(q.h_out, q.d_out, (size_t)T * (1 + P) * sizeof(double),
                         cudaMemcpyDeviceToHost, st));
   CK(c, cudaMemcpyAsync(q.h_out + (size_t)T * (1 + P), c->d_flags, sizeof(int),
@@ -891,8 +893,8 @@ int enqueue_toys(mipwa_ctx* c, cudaStream_t st) {
 }
 
 // Everything a batched evaluation needs, then one launch of the captured graph
-// (or the plain launch sequence when graphs are off).
-int run_toys(mipwa_ctx* c) {
+// (or the plain launch sequence when graphs are off); grad as in enqueue_toys.
+int run_toys(mipwa_ctx* c, bool grad) {
   auto& q = c->tq;
   if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
   if (!c->norm.set) return fail(c, MIPWA_ESTATE, "set_norm_sample must come first");
@@ -918,14 +920,15 @@ int run_toys(mipwa_ctx* c) {
   // (computed outside any stream capture)
   const int occ = toys_blocks_per_sm(c->mode == MIPWA_F32, c->norm.dtype == MIPWA_F32,
                                      c->basis_on, c->norm.weighted && !c->gram_on, c->model,
-                                     q.block);
+                                     q.block, grad);
   if (occ < 1) return fail(c, MIPWA_EINVAL, "no batched kernel with %d threads per block", q.block);
   q.grid = c->sm_count * (q.blocks_per_sm > 0 ? std::min(q.blocks_per_sm, occ) : occ);
   if (q.use_graph) {
+    if (q.exec && q.graph_grad != grad) invalidate_graph(c);
     if (!q.exec) {
       CK(c, cudaStreamSynchronize(c->stream));
       CK(c, cudaStreamBeginCapture(c->own_stream, cudaStreamCaptureModeThreadLocal));
-      rc = enqueue_toys(c, c->own_stream);
+      rc = enqueue_toys(c, c->own_stream, grad);
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(c->own_stream, &g);
       if (rc) {
@@ -934,12 +937,13 @@ int run_toys(mipwa_ctx* c) {
       }
       if (e != cudaSuccess) return fail(c, MIPWA_ECUDA, "stream capture: %s", cudaGetErrorString(e));
       q.graph = g;
+      q.graph_grad = grad;
       CK(c, cudaGraphInstantiate(&q.exec, q.graph, 0));
     }
     CK(c, cudaGraphLaunch(q.exec, c->stream));
     c->launches += c->gram_on ? 4 : 3;
   } else {
-    rc = enqueue_toys(c, c->stream);
+    rc = enqueue_toys(c, c->stream, grad);
     if (rc) return rc;
     c->launches += c->gram_on ? 4 : 3;
   }
@@ -1340,12 +1344,12 @@ bool read_tune_file(const std::string& path, const std::string& key, mipwa_toys_
 // Milliseconds of one batched evaluation at the context's configuration (the
 // best of two after a warm-up that plans and captures).
 int time_toys(mipwa_ctx* c, float* ms) {
-  int rc = run_toys(c);
+  int rc = run_toys(c, true);
   if (rc) return rc;
   *ms = 0.0f;
   for (int rep = 0; rep < 2; ++rep) {
     CK(c, cudaEventRecord(c->ev0, c->stream));
-    rc = run_toys(c);
+    rc = run_toys(c, true);
     if (rc) return rc;
     CK(c, cudaEventRecord(c->ev1, c->stream));
     CK(c, cudaEventSynchronize(c->ev1));
@@ -1414,7 +1418,7 @@ int tune_toys(mipwa_ctx* c, mipwa_toys_config* out, int* n_timed) {
   for (int bs : {128, 256, 512}) {
     if (bs == cur.block) continue;
     if (toys_blocks_per_sm(c->mode == MIPWA_F32, c->norm.dtype == MIPWA_F32, c->basis_on,
-                           weighted, c->model, bs) < 1)
+                           weighted, c->model, bs, true) < 1)
       continue;
     mipwa_toys_config v = cur;
     v.block = bs;
@@ -1423,7 +1427,7 @@ int tune_toys(mipwa_ctx* c, mipwa_toys_config* out, int* n_timed) {
     if (rc) return rc;
   }
   const int occ = toys_blocks_per_sm(c->mode == MIPWA_F32, c->norm.dtype == MIPWA_F32,
-                                     c->basis_on, weighted, c->model, cur.block);
+                                     c->basis_on, weighted, c->model, cur.block, true);
   for (int b = 1; b < occ; ++b) {
     mipwa_toys_config v = cur;
     v.blocks_per_sm = b;
@@ -1773,7 +1777,7 @@ int mipwa_nll_grad_toys(mipwa_ctx* c, const double* params, double* nll, double*
   for (size_t k = 0; k < (size_t)T * P; ++k)
     if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %zu is not finite", k);
   std::memcpy(q.h_params, params, (size_t)T * P * sizeof(double));
-  rc = run_toys(c);
+  rc = run_toys(c, true);
   if (rc) return rc;
   const int flags = *(const int*)(q.h_out + (size_t)T * (1 + P));
   if (flags & kFlagData) return fail(c, MIPWA_ENONPOS, "|A|^2 <= 0 or non-finite for a toy event");
@@ -1784,6 +1788,27 @@ int mipwa_nll_grad_toys(mipwa_ctx* c, const double* params, double* nll, double*
     nll[t] = o[0];
     std::memcpy(grad + (size_t)t * P, o + 1, P * sizeof(double));
   }
+  return MIPWA_OK;
+}
+
+int mipwa_nll_toys(mipwa_ctx* c, const double* params, double* nll) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!params || !nll) return fail(c, MIPWA_EINVAL, "null pointer");
+  if (!c->have_model) return fail(c, MIPWA_ESTATE, "set_model must come first");
+  auto& q = c->tq;
+  const int T = q.n, P = c->n_params;
+  if (T == 0) return fail(c, MIPWA_ESTATE, "set_toys must come first");
+  for (size_t k = 0; k < (size_t)T * P; ++k)
+    if (!std::isfinite(params[k])) return fail(c, MIPWA_EINVAL, "parameter %zu is not finite", k);
+  std::memcpy(q.h_params, params, (size_t)T * P * sizeof(double));
+  rc = run_toys(c, false);
+  if (rc) return rc;
+  const int flags = *(const int*)(q.h_out + (size_t)T * (1 + P));
+  if (flags & kFlagData) return fail(c, MIPWA_ENONPOS, "|A|^2 <= 0 or non-finite for a toy event");
+  if (flags & (kFlagNorm | kFlagIntegral))
+    return fail(c, MIPWA_ENONPOS, "normalisation integral is not positive and finite");
+  for (int t = 0; t < T; ++t) nll[t] = q.h_out[(size_t)t * (1 + P)];
   return MIPWA_OK;
 }
 

@@ -105,14 +105,15 @@ cudaError_t launch_tc_norm(const TcArgs& a, int grid, int mode, cudaStream_t str
 void launch_prepare(const Model& m, const double* params, const double* lu, double* coef,
                     float* coef32, cudaStream_t stream, int n_sets = 1);
 // The batched-toys kernel (block = 128, 256 or 512 threads; weighted
-// normalisation: 256 only) and the per-toy reduction. cudaErrorInvalidValue
-// for a block size without a kernel.
+// normalisation: 256 only) and the per-toy reduction, with the gradient or
+// (grad false) -2 ln L alone. cudaErrorInvalidValue for a block size without
+// a kernel.
 cudaError_t launch_toys(int compute_f32, int ev_f32, const ToyArgs& a, int block, int grid,
-                        cudaStream_t stream);
+                        cudaStream_t stream, bool grad);
 // Resident blocks per SM of the batched-toys kernel that runs for these
 // arguments at this block size (0: no such kernel).
 int toys_blocks_per_sm(int compute_f32, int ev_f32, bool cached, bool weighted, const Model& m,
-                       int block);
+                       int block, bool grad);
 cudaError_t launch_eval(int compute_f32, int ev_f32, bool grad, const EvalArgs& a, int grid,
                         cudaStream_t stream);
 // Column sums of rows_d data rows and rows_n normalisation rows (W wide) into

@@ -207,3 +207,31 @@ def test_toys_config_refusals():
         assert lik.toys_config() == before
     nll, grad = lik.nll_grad_toys(params)
     check_toys(nll, grad, oracle_toys(name, True, tuple(SIZES), 40_000), SIZES, True)
+
+
+@pytest.mark.parametrize("mode", [F64, F32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("cached", [False, True], ids=["direct", "cached"])
+def test_nll_toys_without_gradient(mode, cached):
+    """mipwa_nll_toys (no adjoint work) on the work-list problem: every toy's
+    -2 ln L against the oracle (FP64 1e-12 relative, FP32 1e-2 absolute) and
+    against mipwa_nll_grad_toys, alternating the two calls (the captured graph
+    follows the mode)."""
+    f32 = mode == F32
+    name = "pipipi_n30" if not f32 else "kpipi_n40"
+    spec, pool, offsets, norm, params = toy_problem(name, f32, WL_SIZES, WL_NORM)
+    ref = oracle_toys(name, f32, tuple(WL_SIZES), WL_NORM)
+    lik = make_toys(name, pool, offsets, norm, mode, cached)
+    lik.set_toys_config(norm_chunk=131072, data_chunk=65536)
+    nll = lik.nll_toys(params)
+    for t in range(len(WL_SIZES)):
+        vr = ref[t][0]
+        if f32:
+            assert abs(nll[t] - vr) < 1e-2, (t, nll[t], vr)
+        else:
+            assert abs(nll[t] - vr) <= 1e-12 * max(abs(vr), 1.0), (t, nll[t], vr)
+    nll_g, grad = lik.nll_grad_toys(params)
+    # the same events summed in the same order; FP32: up to FP32 rounding
+    np.testing.assert_allclose(nll_g, nll, rtol=1e-12 if not f32 else 1e-7,
+                               atol=1e-9 if not f32 else 1e-3)
+    check_toys(nll_g, grad, ref, WL_SIZES, f32)
+    np.testing.assert_array_equal(lik.nll_toys(params), nll)
