@@ -625,9 +625,10 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   int cur = -1;
 #pragma unroll
   for (int k = 0; k < 16; ++k) acc[k] = T(0);
-  // computed basis: the next iteration's event is loaded one iteration ahead
-  // (hides the global-load latency behind this iteration's arithmetic; with
-  // the cached basis the extra registers cost more than they hide)
+  // computed basis, and cached basis with PF: the next iteration's event (and
+  // PF: its basis) is loaded one iteration ahead, which hides the global-load
+  // latency behind this iteration's arithmetic (the generic cached kernels
+  // would spill the extra registers)
   EvT e_next{};
   Cplx<T> B_next[PF ? NRc : 1];
   if constexpr ((!CACHED || PF) && U == 1) {
