@@ -96,6 +96,9 @@ def parse():
     ap.add_argument("--reim-steps", type=int, default=10)
     ap.add_argument("--n-toys", type=int, default=256)
     ap.add_argument("--toys-norm", type=int, default=10_000_000)
+    ap.add_argument("--toys-config", type=str, default="",
+                    help="norm_chunk,data_chunk,block,blocks_per_sm for the batched toys "
+                         "instead of the autotuner's choice")
     ap.add_argument("--paper-fit", type=int, default=1,
                     help="run the Sec. 4 workload (K K K, 40 knots, 100K toys) as full fits")
     ap.add_argument("--paper-toys", type=int, default=20,
@@ -411,7 +414,12 @@ def toys_leg(args, stream, rank):
     lik.set_toys(pool, offsets)
     lik.enable_basis_cache(True)
     t_tune = time.perf_counter()
-    best = lik.toys_autotune(params)
+    if args.toys_config:
+        nc, dc, bs, bps = (int(x) for x in args.toys_config.split(","))
+        lik.set_toys_config(norm_chunk=nc, data_chunk=dc, block=bs, blocks_per_sm=bps)
+        best = dict(lik.toys_config(), n_timed=0, given=True)
+    else:
+        best = lik.toys_autotune(params)
     t_tune = time.perf_counter() - t_tune
     lik.nll_grad_toys(params)
     launches0 = lik.launch_count()
