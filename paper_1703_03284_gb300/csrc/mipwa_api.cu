@@ -592,6 +592,37 @@ int resort(mipwa_ctx* c, mipwa_ctx::Sample& smp) {
   return MIPWA_OK;
 }
 
+// Group each toy's events by spline cell within the toy's own range
+// [offsets[t], offsets[t+1]) (the batched kernel then sums the spline adjoint
+// of a toy's data events in registers, as for one sorted sample); after
+// set_toys and after set_model.
+int sort_toys(mipwa_ctx* c) {
+  mipwa_ctx::Sample& smp = c->toys;
+  auto& q = c->tq;
+  if (!smp.set || !c->have_model || q.n == 0 || smp.n < 2) return MIPWA_OK;
+  const size_t eb = ev_bytes(smp.dtype);
+  int64_t nmax = 0;
+  for (int t = 0; t < q.n; ++t) nmax = std::max(nmax, q.offsets[t + 1] - q.offsets[t]);
+  int rc = ensure(c, &smp.spare, &smp.spare_cap, (size_t)nmax * eb);
+  if (!rc) rc = ensure_sortwork(c);
+  if (rc) return rc;
+  CK(c, cudaStreamWaitEvent(c->stream, smp.spare_free, 0));
+  for (int t = 0; t < q.n; ++t) {
+    const int64_t nt = q.offsets[t + 1] - q.offsets[t];
+    if (!sortable(nt)) continue;
+    char* range = (char*)smp.cur + (size_t)q.offsets[t] * eb;
+    CK(c, launch_sort(smp.dtype == MIPWA_F32, c->model, range, nt, smp.spare, range,
+                      c->d_sortwork, c->stream));
+    c->launches += kSortLaunches;
+  }
+  CK(c, cudaEventRecord(smp.spare_free, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  smp.gen++;
+  smp.basis_valid = false;
+  invalidate_graph(c);
+  return MIPWA_OK;
+}
+
 int evaluate(mipwa_ctx* c, const double* params, double* nll, double* grad, bool want_grad) {
   int rc = check_ctx(c);
   if (rc) return rc;
@@ -1619,7 +1650,9 @@ int mipwa_set_model(mipwa_ctx* c, const mipwa_resonance* res, int n_res, const d
   invalidate_basis(c);
   rc = resort(c, c->data);
   if (rc) return rc;
-  return resort(c, c->norm);
+  rc = resort(c, c->norm);
+  if (rc) return rc;
+  return sort_toys(c);
 }
 
 int mipwa_set_resonances(mipwa_ctx* c, const mipwa_resonance* res, int n_res) {
@@ -1763,7 +1796,7 @@ int mipwa_set_toys(mipwa_ctx* c, const void* ptr, int64_t n_total, int dtype, in
   q.planned = false;
   invalidate_graph(c);
   CK(c, cudaStreamSynchronize(c->stream));
-  return MIPWA_OK;
+  return sort_toys(c);
 }
 
 int mipwa_nll_grad_toys(mipwa_ctx* c, const double* params, double* nll, double* grad) {
