@@ -581,7 +581,7 @@ __device__ void finalize_rows(SmemCommon& sm, const Model& m, const double* lu,
 // spline polynomial adjoints (8 (N-1))]. The per-evaluation model data must be
 // staged in sm; the bins are zeroed here. Every thread of the block calls this.
 template <typename T, typename EvT, bool GRAD, int SIG, bool CACHED, bool BWG = false,
-          bool WN = false, int U = 1, bool WF = false>
+          bool WN = false, int U = 1>
 __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
                                  const Cplx<T>* cached, int64_t n, int64_t first, int64_t end,
                                  int64_t stride, bool is_data, double* row, int* flags,
@@ -615,16 +615,17 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
   int iter = 0;
   // FP32 form: the spline adjoint of the thread's events is summed in
   // registers while they stay in one spline cell (events are grouped by cell
-  // and a thread's consecutive events are a block apart); every kFlushIters
-  // iterations (counted by iter) the warp adds its sums to the shared bins
-  // (one reduce-scatter when the warp shares the cell), just before the
-  // shared bins go to FP64, and a lane whose cell changes adds its own.
-  // (Measured on the 40-knot workload: 64 iterations 0.8 % faster than 16.)
-  // WF (small samples, the toys': a cell holds a few hundred events, so a
-  // thread, whose events are a block apart, changes cell every few events):
-  // the warp flushes together whenever one of its lanes changes cell, one
-  // reduce-scatter while the lanes share the cell they leave, instead of
-  // each lane adding its 16 sums to bins that the other lanes add to too.
+  // and a thread's consecutive events are a block apart). The warp adds its
+  // sums to the shared bins together: whenever one of its lanes moves to
+  // another cell, and every kFlushIters iterations (counted by iter), just
+  // before the shared bins go to FP64; one reduce-scatter while the lanes
+  // share the cell they leave (grouped events move on together), else lane by
+  // lane. (Lanes flushing on their own into the bins of the one cell they all
+  // leave serialise on the same shared-memory words: with that, 10^6 + 10^6
+  // events took 0.366 ms instead of 0.165 ms, where a cell holds about 1,300
+  // events and a thread changes cell every ten events, and 10^8 + 10^8 0.9 %
+  // longer. Measured on the 40-knot workload: flushing every 64 iterations
+  // 0.8 % faster than every 16.)
   constexpr bool kThreadBins = std::is_same<T, float>::value;
   T acc[16];
   int cur = -1;
@@ -701,7 +702,7 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
       }
       bad |= ok ? 0 : 1;
     }
-    if constexpr (GRAD && kThreadBins && WF) {
+    if constexpr (GRAD && kThreadBins) {
       const int key = ok ? (sw.j12() << 6) | sw.j13() : cur;
       if (__any_sync(0xffffffffu, key != cur)) {
         flush_bins_warp(sm, cur, acc);
@@ -735,13 +736,6 @@ __device__ void accumulate_range(EvalSmem<T>& sm, const Model& m, const EvT* ev,
         }
         const bool reim = SIG == 0 ? m.reim != 0 : sig_reim(SIG);
         if constexpr (kThreadBins) {
-          if constexpr (!WF) {
-            const int key = (sw.j12() << 6) | sw.j13();
-            if (key != cur) {
-              if (cur >= 0) flush_bins(sm, cur, acc);
-              cur = key;
-            }
-          }
           if constexpr (CACHED) {
             swave_adjoint_add2(sw, reim, Aw, acc);
           } else {

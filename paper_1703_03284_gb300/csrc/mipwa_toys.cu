@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(BS, (kToyMinBlocks<T, BS>)) toys_kernel(const 
     const Cplx<T>* cached =
         reinterpret_cast<const Cplx<T>*>(it.is_data ? a.basis_data : a.basis_norm);
     const int64_t n = it.is_data ? a.n_data : a.n_norm;
-    accumulate_range<T, EvT, GRAD, SIG, CACHED, false, WN, 1, true>(
+    accumulate_range<T, EvT, GRAD, SIG, CACHED, false, WN>(
         sm, m, ev, cached, n, it.start, it.end, (int64_t)BS, it.is_data != 0,
         a.partials + (size_t)it.row * W, a.flags, a.coef + (size_t)it.toy * cs, a.norm_w);
   }
