@@ -431,9 +431,10 @@ __device__ __forceinline__ void flush_bins(EvalSmem<T>& sm, int key, T (&acc)[16
   }
 }
 
-// The warp's register sums into the shared bins: one reduce-scatter when every
-// lane holding sums is in the same cell, else one lane at a time. All lanes of
-// the warp call this together; cur < 0 means "no sums".
+// The warp's register sums into the shared bins: one reduce-scatter per cell
+// that its lanes hold sums of (at most four cells, the common case of a warp
+// across a cell boundary), else one lane at a time. All lanes of the warp call
+// this together; cur < 0 means "no sums".
 template <typename T>
 __device__ __forceinline__ void flush_bins_warp(EvalSmem<T>& sm, int cur, T (&acc)[16]) {
   constexpr unsigned full = 0xffffffffu;
@@ -450,8 +451,28 @@ __device__ __forceinline__ void flush_bins_warp(EvalSmem<T>& sm, int cur, T (&ac
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = T(0);
-  } else if (cur >= 0) {
-    flush_bins(sm, cur, acc);
+  } else {
+    const int lane = threadIdx.x & 31;
+    unsigned todo = have;
+    for (int round = 0; round < 4 && todo; ++round) {
+      const int kk = __shfl_sync(full, cur, __ffs(todo) - 1);
+      const bool mine = cur == kk;
+      T part[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) part[k] = mine ? acc[k] : T(0);
+      const T tot = reduce_scatter16(part, lane);
+      if ((lane & 1) == 0) {
+        const int idx = lane >> 1;
+        const int j = idx < 8 ? (kk >> 6) : (kk & 63);
+        bin_add(sm, j * 8 + (idx & 7), tot);
+      }
+      if (mine) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[k] = T(0);
+      }
+      todo &= ~__ballot_sync(full, mine);
+    }
+    if ((todo >> lane) & 1u) flush_bins(sm, cur, acc);
   }
 }
 
