@@ -71,13 +71,13 @@ def _measured_hbm_gbs() -> float:
 
 HBM_GBS = _measured_hbm_gbs()
 # DRAM bytes (read + write) of the fused FP32 NLL+gradient kernel per event
-# processed, from one ncu capture on 2e7 + 2e7 events (320.07 MB read + 3.85
+# processed, from one ncu capture on 2e7 + 2e7 events (320.26 MB read + 4.68
 # MB written per launch); a launch's traffic is this times its events. None
 # once the kernel has changed since the capture.
-TRAFFIC_PER_EVENT = (320.072448e6 + 3.845888e6) / 4e7
-# The same for the cached-basis kernel (960.44 MB read + 5.84 MB written for
+TRAFFIC_PER_EVENT = (320.259584e6 + 4.678144e6) / 4e7
+# The same for the cached-basis kernel (960.11 MB read + 6.00 MB written for
 # 2e7 + 2e7 events with their cached Breit-Wigner terms).
-TRAFFIC_PER_EVENT_CACHED = (960.442624e6 + 5.843968e6) / 4e7
+TRAFFIC_PER_EVENT_CACHED = (960.105472e6 + 6.001408e6) / 4e7
 
 
 def parse():
