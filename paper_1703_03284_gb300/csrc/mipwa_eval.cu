@@ -20,9 +20,12 @@ namespace mipwa {
 
 // Resident threads per SM the FP32 kernels are compiled for, in blocks of
 // kEvalThreads: 768 (up to 85 registers) for the NLL + gradient with computed
-// Breit-Wigner terms, 1024 (64 registers) otherwise. Measured on the 40-knot
-// workload: the gradient kernels 1.2 % (magnitude/phase) and 3 % (Re/Im)
-// faster with 768 than 1024, the cached-basis one 12 % slower. Blocks of 128
+// Breit-Wigner terms, 896 (73) with the cached basis, 1024 (64) for the NLL
+// alone. Measured on the 40-knot workload: the gradient kernels 1.2 %
+// (magnitude/phase) and 3 % (Re/Im) faster with 768 than 1024; the cached-
+// basis one 12 % slower with 768 than 1024 threads of 256-thread blocks, and
+// with 128-thread blocks and the warp-wide flushes 1.7 % faster with 896 than
+// 1024. Blocks of 128
 // threads: 1.9 % faster than 256 at the same 24 warps per SM (a block's
 // periodic barrier holds fewer warps); 7 blocks 1.3 %, 8 blocks (64
 // registers) 0.7 % slower than that. The NLL-only kernel runs on the gradient
@@ -30,7 +33,7 @@ namespace mipwa {
 // identically), 1.7 % slower than on its own.
 template <typename T, bool GRAD, bool CACHED>
 constexpr int kEvalMinBlocks =
-    sizeof(T) == 4 ? (GRAD && !CACHED ? 768 : 1024) / kEvalThreads : 1;
+    sizeof(T) == 4 ? (GRAD ? (CACHED ? 896 : 768) : 1024) / kEvalThreads : 1;
 
 // Events per thread per loop iteration of the FP32 NLL + gradient kernels
 // with computed Breit-Wigner terms (accumulate_range's U).
