@@ -75,9 +75,9 @@ HBM_GBS = _measured_hbm_gbs()
 # MB written per launch); a launch's traffic is this times its events. None
 # once the kernel has changed since the capture.
 TRAFFIC_PER_EVENT = (320.259584e6 + 4.678144e6) / 4e7
-# The same for the cached-basis kernel (960.11 MB read + 6.00 MB written for
+# The same for the cached-basis kernel (960.15 MB read + 5.28 MB written for
 # 2e7 + 2e7 events with their cached Breit-Wigner terms).
-TRAFFIC_PER_EVENT_CACHED = (960.105472e6 + 6.001408e6) / 4e7
+TRAFFIC_PER_EVENT_CACHED = (960.150272e6 + 5.282816e6) / 4e7
 
 
 def parse():
